@@ -1,0 +1,481 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a value the
+paper prints (Table A.1), a closed form (equilibrium moments, exact lattice
+averages of the Taylor-Green field, the linear internal-wave frequency of the
+Boussinesq system, the viscous decay of a shear wave), an exact invariant
+(mass, momentum and scalar budgets, symmetries, translation, power-of-two
+rescaling) or a special case that reduces to plain BGK. A plausible mistake in
+the oracle (a dropped term, a wrong sign or index, a swapped G and beta) fails
+at least one of them.
+"""
+from fractions import Fraction
+import math
+import os
+
+import numpy as np
+import pytest
+
+import stgv_inputs as I
+from oracle import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+LAM = 2.0 ** -10  # G / N split used by the lattice mapping
+
+
+def _read_table_a1():
+    rows = []
+    with open(os.path.join(GOLDEN, "table_a1_stencils.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            name, cs2, m, count, w = line.split()
+            rows.append((int(name[3:]), Fraction(cs2), int(m), int(count), Fraction(w)))
+    return rows
+
+
+def test_stencils_match_table_a1():
+    """Table A.1: c_s^2, group sizes and weights of D3Q7/15/19/27."""
+    rows = _read_table_a1()
+    for q in (7, 15, 19, 27):
+        e, w, cs2 = O.stencil(q)
+        assert len(w) == q
+        mine = [r for r in rows if r[0] == q]
+        assert abs(cs2 - float(mine[0][1])) < 1e-16
+        m2 = (e ** 2).sum(axis=1)
+        for _, _, m, count, wt in mine:
+            sel = m2 == m
+            assert sel.sum() == count
+            assert np.all(np.abs(w[sel] - float(wt)) < 1e-16)
+        assert sum(r[3] for r in mine) == q
+        # every velocity is distinct and its opposite is present
+        codes = {tuple(v) for v in e}
+        assert len(codes) == q
+        assert all(tuple(-v) in codes for v in e)
+
+
+@pytest.mark.parametrize("q", [7, 15, 19, 27])
+def test_stencil_isotropy(q):
+    """Lattice tensor identities: sum w = 1, odd moments vanish, second moment
+    cs^2 delta; fourth moment cs^4 (dd + dd + dd) for Q15/19/27, not for Q7."""
+    e, w, cs2 = O.stencil(q)
+    e = e.astype(float)
+    d = np.eye(3)
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.allclose(np.einsum("i,ia->a", w, e), 0.0, atol=1e-16)
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, e, e), cs2 * d, atol=1e-15)
+    assert np.allclose(np.einsum("i,ia,ib,ic->abc", w, e, e, e), 0.0, atol=1e-16)
+    m4 = np.einsum("i,ia,ib,ic,id->abcd", w, e, e, e, e)
+    iso = cs2 ** 2 * (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+                      + np.einsum("ad,bc->abcd", d, d))
+    if q == 7:
+        assert not np.allclose(m4, iso, atol=1e-6)
+    else:
+        assert np.allclose(m4, iso, atol=1e-15)
+
+
+@pytest.mark.parametrize("q", [7, 15, 19, 27])
+def test_equilibrium_moments(q):
+    """Eq. 9: sum f_eq = rho, sum e f_eq = rho u, and (Q15/19/27)
+    sum e e f_eq = rho u u + rho cs^2 I, exactly up to round-off."""
+    e, w, cs2 = O.stencil(q)
+    rng = np.random.default_rng(1234 + q)
+    for _ in range(20):
+        rho = 1.0 + 0.1 * rng.uniform(-1, 1)
+        u = 0.1 * rng.uniform(-1, 1, 3)
+        feq = O.equilibrium(q, rho, u)
+        assert abs(feq.sum() - rho) < 1e-15
+        assert np.allclose(feq @ e, rho * u, atol=1e-16)
+        if q != 7:
+            pi = np.einsum("i,ia,ib->ab", feq, e, e)
+            assert np.allclose(pi, rho * np.outer(u, u) + rho * cs2 * np.eye(3), atol=1e-15)
+
+
+def test_physics_mapping():
+    """Section 2.4 / Eq. 19 mapping: box 2 pi = n nodes, Re = U L / nu,
+    Fr = U / (N L), Sc = nu / D, tau = nu / cs^2 + 1/2 (Eqs. 8, 14), and
+    N^2 = -(G / rho0) d rho_b / dz (Eq. 19)."""
+    for n, qf, qg, Re, Fr, Sc, U0 in [(32, 27, 19, 100, 0.5, 1.0, 0.04),
+                                      (256, 27, 19, 800, 0.1, 1.0, 0.04),
+                                      (128, 19, 7, 400, 0.1, 0.7, 0.0577)]:
+        p = O.params_from_physics(n, qf, qg, "sc", Re, Fr, Sc, U0)
+        L = n / (2 * math.pi)
+        nu = U0 * L / Re
+        cs2g = 0.25 if qg == 7 else 1.0 / 3.0
+        assert abs(p.tau_f - (3 * nu + 0.5)) < 1e-15
+        assert abs(p.tau_g - (nu / Sc / cs2g + 0.5)) < 1e-15
+        N = U0 / (Fr * L)
+        assert abs(-p.G * p.beta / p.rho0 - N * N) < 1e-18
+        assert p.rho0 == 1.0
+        assert abs(p.G / N - LAM) < 1e-15
+
+
+def _random_sim(nx, ny, nz, qf, qg, forcing, seed, G=2e-3 * LAM, beta=None, tau_f=0.55,
+                tau_g=0.56, scalar_mode=0, sc_shift=1.0, rho0=1.0, rho_p_amp=None):
+    N = 2e-3
+    if beta is None:
+        beta = -N * N * rho0 / G if G != 0 else 0.0
+    p = O.lattice_params(nx, ny, nz, qf, qg, forcing, tau_f, tau_g, G, beta, rho0=rho0,
+                         scalar_mode=scalar_mode, sc_shift=sc_shift)
+    s = O.OracleSim(p)
+    n3 = nx * ny * nz
+    rp_amp = (0.02 / LAM) if rho_p_amp is None else rho_p_amp
+    rho, u, rp = I.random_fields(nx, ny, nz, seed, 0.05, 0.01, rp_amp)
+    s.init_fields(rho, u, rp, I.neq_noise(n3, seed + 1), I.neq_noise(n3, seed + 2), 1e-3)
+    return s
+
+
+@pytest.mark.parametrize("forcing", ["guo", "sc", "edm", "hcz"])
+@pytest.mark.parametrize("pair", [(27, 19), (19, 7)])
+def test_mass_and_momentum_budget(forcing, pair):
+    """Eqs. 5-8 with forcing: total mass sum_x sum_i f_i is conserved and the
+    lattice momentum sum_x sum_i e_i f_i gains exactly sum_x F per step
+    (Eq. 18), for every forcing scheme."""
+    s = _random_sim(6, 5, 4, pair[0], pair[1], forcing, seed=11, G=3e-3)
+    for _ in range(3):
+        d0 = s.diagnostics()
+        _, _, rp = s.fields()
+        Fz = -s.params.G * rp.sum()
+        s.step(1)
+        d1 = s.diagnostics()
+        assert abs(d1["mass_f"] - d0["mass_f"]) < 1e-12
+        assert abs(d1["mom_x"] - d0["mom_x"]) < 1e-13
+        assert abs(d1["mom_y"] - d0["mom_y"]) < 1e-13
+        assert abs((d1["mom_z"] - d0["mom_z"]) - Fz) < 1e-13 * (1 + abs(Fz))
+
+
+def test_shan_chen_printed_shift_halves_gravity():
+    """Eq. 10 as printed (tau_f F / (2 rho)) adds only F/2 of momentum per step;
+    the standard Shan-Chen shift (tau_f F / rho) adds F."""
+    for shift, frac in [(0.5, 0.5), (1.0, 1.0)]:
+        s = _random_sim(5, 4, 3, 27, 19, "sc", seed=5, G=3e-3, sc_shift=shift)
+        d0 = s.diagnostics()
+        _, _, rp = s.fields()
+        Fz = -s.params.G * rp.sum()
+        s.step(1)
+        d1 = s.diagnostics()
+        assert abs((d1["mom_z"] - d0["mom_z"]) - frac * Fz) < 1e-13 * (1 + abs(Fz))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("qg", [19, 7])
+def test_scalar_budget(mode, qg):
+    """Eqs. 11-17 scalar bookkeeping. With sigma = sum g, rho' + rho0 = sigma +
+    c_mom sum S (Eq. 16) and g* = g - (g - g_eq)/tau_g + c_lbe S_i, the total
+    sum_x sum_i g changes per step by exactly sum_x (c_lbe + c_mom / tau_g) sum_i S_i,
+    sum_i S_i = -u_z beta (Eq. 12). Printed pair: c_lbe = 1, c_mom =
+    (1 - 1/(2 tau_g))/2; Chai-Shi pair: c_lbe = 1 - 1/(2 tau_g), c_mom = 1/2 (net 1)."""
+    s = _random_sim(5, 4, 6, 27, qg, "guo", seed=21, G=3e-3, scalar_mode=mode, tau_g=0.7)
+    tg = s.params.tau_g
+    if mode == 0:
+        c_lbe, c_mom = 1.0, 0.5 * (1 - 1 / (2 * tg))
+    else:
+        c_lbe, c_mom = 1 - 1 / (2 * tg), 0.5
+    for _ in range(3):
+        d0 = s.diagnostics()
+        _, u, _ = s.fields()
+        src = (-u[2] * s.params.beta).sum()
+        s.step(1)
+        d1 = s.diagnostics()
+        expect = (c_lbe + c_mom / tg) * src
+        assert abs((d1["mass_g"] - d0["mass_g"]) - expect) < 1e-12 * (1 + abs(expect)), (
+            d1["mass_g"] - d0["mass_g"], expect)
+
+
+def test_rest_state_is_fixed_point():
+    """u = 0, rho = rho0, rho' = 0 is an exact steady state (F = 0, S = 0)."""
+    for forcing in ("guo", "sc", "edm", "hcz"):
+        p = O.lattice_params(4, 4, 4, 27, 19, forcing, 0.51, 0.52, 1e-5, -4.0)
+        s = O.OracleSim(p)
+        s.init_fields(np.ones(64), np.zeros((3, 64)), np.zeros(64))
+        f0, g0 = s.populations()
+        s.step(7)
+        f1, g1 = s.populations()
+        assert np.max(np.abs(f1 - f0)) < 1e-15
+        assert np.max(np.abs(g1 - g0)) < 1e-15
+
+
+def test_zero_force_reduces_all_schemes_to_bgk():
+    """With G = 0 there is no force and Guo, SC, EDM and HCZ are all plain BGK."""
+    ref = None
+    for forcing in ("guo", "sc", "edm", "hcz"):
+        s = _random_sim(4, 3, 5, 27, 19, forcing, seed=3, G=0.0, beta=-1e-3)
+        s.step(4)
+        f, g = s.populations()
+        if ref is None:
+            ref = (f, g)
+        else:
+            assert np.max(np.abs(f - ref[0])) < 1e-16
+            assert np.max(np.abs(g - ref[1])) < 1e-16
+
+
+@pytest.mark.parametrize("pair", [(27, 19), (19, 7)])
+def test_single_node_relaxation(pair):
+    """On a 1^3 periodic domain streaming is the identity. With G = 0 and a
+    non-equilibrium part that carries no mass or momentum, BGK (Eqs. 8, 14)
+    scales it by exactly (1 - 1/tau) each step."""
+    qf, qg = pair
+    tau_f, tau_g = 0.8, 1.3
+    p = O.lattice_params(1, 1, 1, qf, qg, "guo", tau_f, tau_g, 0.0, 0.0)
+    s = O.OracleSim(p)
+    ef, wf, _ = O.stencil(qf)
+    eg, wg, _ = O.stencil(qg)
+    rho, u, rp = 1.02, np.array([0.03, -0.02, 0.01]), 0.3
+    feq = O.equilibrium(qf, rho, u)
+    theta = O.equilibrium(qg, 1.0, u)
+    rng = np.random.default_rng(7)
+    df = rng.uniform(-1, 1, qf) * wf * 1e-3
+    # project out mass and momentum (orthogonal projection onto the null space
+    # of the zeroth and first moments)
+    A = np.vstack([np.ones(qf), ef.T.astype(float)])
+    df -= A.T @ np.linalg.solve(A @ A.T, A @ df)
+    assert abs(df.sum()) < 1e-18 and np.allclose(ef.T @ df, 0, atol=1e-18)
+    dg = rng.uniform(-1, 1, qg) * wg * 1e-3
+    dg -= wg * dg.sum() / wg.sum()
+    s.set_populations(feq + df, (rp + 1.0) * theta + dg)
+    for t in range(1, 6):
+        s.step(1)
+        f, g = s.populations()
+        # round-off of rho, u and f_eq accumulates to a few 1e-16 per step
+        assert np.allclose(f[:, 0] - feq, (1 - 1 / tau_f) ** t * df, atol=2e-15, rtol=1e-10)
+        assert np.allclose(g[:, 0] - (rp + 1.0) * theta, (1 - 1 / tau_g) ** t * dg,
+                           atol=2e-15, rtol=1e-10)
+
+
+def _shear_rate(n, tau):
+    p = O.lattice_params(n, n, n, 27, 19, "guo", tau, 0.6, 0.0, 0.0)
+    s = O.OracleSim(p)
+    s.init_fields(*I.shear_wave_fields(n, 1e-3))
+    nu = (tau - 0.5) / 3.0
+    k = 2 * np.pi / n
+    t0, t1 = int(0.1 / (nu * k * k)), int(1.0 / (nu * k * k))
+    s.step(t0)
+    e0 = s.diagnostics()["Ek"]
+    s.step(t1 - t0)
+    e1 = s.diagnostics()["Ek"]
+    return np.log(e0 / e1) / (t1 - t0) / (2 * nu * k * k) - 1.0
+
+
+def test_shear_wave_viscous_decay():
+    """A transverse mode u_x = A sin(k z) of the Navier-Stokes limit decays as
+    KE ~ exp(-2 nu k^2 t) with nu = cs^2 (tau_f - 1/2) (Eq. 8). The lattice
+    error is second order in k: |err| < 2e-3 at n = 32 and ~4x at n = 16."""
+    e32 = _shear_rate(32, 0.9)
+    e16 = _shear_rate(16, 0.9)
+    assert abs(e32) < 2e-3
+    assert 3.0 < e16 / e32 < 5.0
+
+
+def _internal_wave_omega(n, N, tau_g, forcing="guo", scalar_mode=0, sc_shift=1.0, every=4):
+    from scipy.optimize import curve_fit
+
+    G = LAM * N
+    p = O.lattice_params(n, n, n, 27, 19, forcing, 0.506, tau_g, G, -N * N / G,
+                         scalar_mode=scalar_mode, sc_shift=sc_shift)
+    s = O.OracleSim(p)
+    B = 1e-4 / LAM
+    s.init_fields(*I.density_mode_fields(n, B))
+    X, Y, Z = I.grid_axes(n)
+    c = np.cos(X + Z)
+    wb = N / np.sqrt(2.0)
+    T = int(1.25 * 2 * np.pi / wb)
+    ts, ps = [], []
+    for _ in range(0, T, every):
+        _, _, r = s.fields()
+        ps.append(r @ c / (c @ c) / B)
+        ts.append(s.step_count)
+        s.step(every)
+    model = lambda t, a, w, ph, g: a * np.cos(w * t + ph) * np.exp(-g * t)
+    popt, _ = curve_fit(model, np.array(ts, float), np.array(ps), p0=[1, wb, 0, 1e-5])
+    return popt[1] / wb
+
+
+def test_internal_wave_frequency():
+    """Linearised Eqs. 2, 4, 18, 19: a density mode with wavevector k = (1, 0, 1)
+    2 pi / n oscillates at omega = N k_h / |k| = N / sqrt(2); within 1% at n = 32."""
+    r = _internal_wave_omega(32, 0.02, 0.506, "guo")
+    assert abs(r - 1.0) < 0.01, r
+
+
+def test_internal_wave_frequency_sc_and_printed_shift():
+    """Standard Shan-Chen (tau_f F / rho) gives N k_h/|k|; the shift printed in
+    Eq. 10 (tau_f F / (2 rho)) halves gravity, so omega drops by 1/sqrt(2)."""
+    r_sc = _internal_wave_omega(16, 0.02, 0.506, "sc", every=2)
+    r_half = _internal_wave_omega(16, 0.02, 0.506, "sc", sc_shift=0.5, every=2)
+    assert abs(r_sc - 1.0) < 0.03
+    assert abs(r_half / r_sc - 1 / np.sqrt(2.0)) < 0.01
+
+
+def test_scalar_pair_frequency_ratio():
+    """The printed scalar pair (Eqs. 11 and 16) feeds sum S (1 + (2 tau_g - 1) /
+    (4 tau_g^2)) into rho' per step, the Chai-Shi pair exactly sum S, so the
+    wave frequencies differ by sqrt(1 + (2 tau_g - 1) / (4 tau_g^2))."""
+    tg = 0.6
+    r0 = _internal_wave_omega(16, 0.02, tg, "guo", scalar_mode=0, every=2)
+    r1 = _internal_wave_omega(16, 0.02, tg, "guo", scalar_mode=1, every=2)
+    expect = np.sqrt(1 + (2 * tg - 1) / (4 * tg * tg))  # 1.067 at tau_g = 0.6
+    # n = 16 carries ~1% of second-order lattice error in the ratio
+    assert abs(r0 / r1 / expect - 1) < 0.012, (r0 / r1, expect)
+
+
+@pytest.mark.parametrize("n", [4, 12, 32])
+def test_tgv_initial_energy_and_dissipation(n):
+    """Eq. 20 on the vertex grid x_i = 2 pi i / n: discrete orthogonality gives
+    E_k(0) = U0^2 / 8 exactly, E_p(0) = 0, and the central-difference vorticity
+    average <|curl u|^2> = sin^2(2 pi / n) * 3 U0^2 / 4 (Eq. 25)."""
+    U0 = 0.04
+    p = O.params_from_physics(n, 27, 19, "guo", 100.0, 0.5, 1.0, U0)
+    s = O.OracleSim(p)
+    s.init_fields(*I.tgv_fields(n, U0))
+    d = s.diagnostics()
+    assert abs(d["Ek"] / (U0 ** 2 / 8) - 1) < 1e-13
+    assert d["Ep"] < 1e-30  # rho' = 0 up to the round-off of sum_i Theta_i = 1
+    nu = (p.tau_f - 0.5) / 3
+    k = 2 * np.pi / n
+    assert abs(d["eps_k_curl"] / (nu * np.sin(k) ** 2 * 0.75 * U0 ** 2) - 1) < 1e-12
+    assert abs(d["mass_f"] / n ** 3 - 1) < 1e-13
+    assert abs(d["eps_k"]) < 1e-25  # equilibrium start: no non-equilibrium stress
+
+
+def test_density_mode_gradient_estimator():
+    """Eq. 26 by central differences: for rho' = B cos(kx x + kz z) on the lattice,
+    <|grad rho'|^2> = B^2 (sin^2 kx + sin^2 kz) / 2 exactly, so eps_p =
+    D (G/N)^2 B^2 (sin^2 kx + sin^2 kz) / 2 / rho0^2."""
+    n, B = 12, 3.0
+    # passive scalar (G = beta = 0, (G/N)^2 taken as 1) so that rho' is exactly the input
+    p = O.lattice_params(n, n, n, 27, 19, "guo", 0.6, 0.7, 0.0, 0.0)
+    s = O.OracleSim(p)
+    s.init_fields(*I.density_mode_fields(n, B, kx=1, kz=2))
+    d = s.diagnostics()
+    D = (0.7 - 0.5) / 3.0
+    k = 2 * np.pi / n
+    expect = D * B ** 2 * (np.sin(k) ** 2 + np.sin(2 * k) ** 2) / 2
+    assert abs(d["eps_p"] / expect - 1) < 1e-12
+    assert abs(d["Ep"] / (0.5 * B ** 2 * 0.5) - 1) < 1e-12
+
+
+def test_shear_wave_nonequilibrium_dissipation():
+    """The non-equilibrium second moment estimates the strain rate: for a decaying
+    shear wave eps_k = 2 nu <S:S> = 2 nu k^2 E_k (to the second-order lattice
+    error), and the central-difference Eq. 25 gives the same times sin^2(k)/k^2."""
+    n, tau = 32, 0.6
+    p = O.lattice_params(n, n, n, 27, 19, "guo", tau, 0.6, 0.0, 0.0)
+    s = O.OracleSim(p)
+    s.init_fields(*I.shear_wave_fields(n, 1e-3))
+    s.step(60)
+    d = s.diagnostics()
+    nu = (tau - 0.5) / 3
+    k = 2 * np.pi / n
+    assert abs(d["eps_k"] / (2 * nu * k * k * d["Ek"]) - 1) < 0.01
+    assert abs(d["eps_k_curl"] / (2 * nu * np.sin(k) ** 2 * d["Ek"]) - 1) < 0.003
+
+
+def _mirror(a, n, axis):
+    """Index map i -> (n - i) mod n along one axis of a flat (z, y, x) field."""
+    a3 = a.reshape(n, n, n)
+    ax = {0: 2, 1: 1, 2: 0}[axis]
+    return np.roll(np.flip(a3, axis=ax), 1, axis=ax).ravel()
+
+
+def test_tgv_mirror_symmetries():
+    """Eq. 20 is odd/even under x -> -x and y -> -y and the update preserves this
+    to round-off. The z-mirror flips the sign of u_z and of the buoyancy part of
+    rho' (Eqs. 4, 18) but not of the rho0 share of g_eq (Eq. 15), so it holds as
+    a two-run identity: since the scalar update is linear in (g, rho0, S), the
+    run with rho0 -> -rho0 started from the mirrored state equals the mirrored
+    run with rho' and g negated."""
+    n, U0 = 12, 0.04
+    p = O.params_from_physics(n, 27, 19, "sc", 100.0, 0.3, 1.0, U0)
+    s = O.OracleSim(p)
+    s.init_fields(*I.tgv_fields(n, U0))
+    s.step(40)
+    rho, u, rp = s.fields()
+    scale = np.abs(u).max()
+    rscale = np.abs(rp).max()
+    assert rscale > 0
+    # x -> -x: u_x odd, u_y, u_z, rho' even
+    assert np.max(np.abs(_mirror(u[0], n, 0) + u[0])) < 1e-12 * scale
+    assert np.max(np.abs(_mirror(u[1], n, 0) - u[1])) < 1e-12 * scale
+    assert np.max(np.abs(_mirror(u[2], n, 0) - u[2])) < 1e-12 * scale
+    assert np.max(np.abs(_mirror(rp, n, 0) - rp)) < 1e-12 * rscale
+    # y -> -y: u_y odd
+    assert np.max(np.abs(_mirror(u[1], n, 1) + u[1])) < 1e-12 * scale
+    assert np.max(np.abs(_mirror(u[0], n, 1) - u[0])) < 1e-12 * scale
+    assert np.max(np.abs(_mirror(rp, n, 1) - rp)) < 1e-12 * rscale
+    # z -> -z with rho0 -> -rho0
+    pm = O.params_from_physics(n, 27, 19, "sc", 100.0, 0.3, 1.0, U0)
+    pm.rho0 = -1.0
+    sm = O.OracleSim(pm)
+    r0, u0, rp0 = I.tgv_fields(n, U0)
+    u0m = np.stack([_mirror(u0[0], n, 2), _mirror(u0[1], n, 2), -_mirror(u0[2], n, 2)])
+    sm.init_fields(_mirror(r0, n, 2), u0m, -_mirror(rp0, n, 2))
+    sm.step(40)
+    _, um, rpm = sm.fields()
+    assert np.max(np.abs(_mirror(um[0], n, 2) - u[0])) < 1e-12 * scale
+    assert np.max(np.abs(_mirror(um[1], n, 2) - u[1])) < 1e-12 * scale
+    assert np.max(np.abs(_mirror(um[2], n, 2) + u[2])) < 1e-12 * scale
+    assert np.max(np.abs(_mirror(rpm, n, 2) + rp)) < 1e-12 * rscale
+    # and the single run is not z-symmetric: the rho0 share of g breaks it
+    assert np.max(np.abs(_mirror(rp, n, 2) + rp)) > 1e-6 * rscale
+
+
+def test_translation_commutes_with_step():
+    """The update is the same at every node: shifting the initial fields by an
+    integer lattice vector and stepping equals stepping and then shifting."""
+    nx, ny, nz = 6, 5, 4
+    n3 = nx * ny * nz
+    rho, u, rp = I.random_fields(nx, ny, nz, 77, 0.05, 0.01, 0.02 / LAM)
+    xf, xg = I.neq_noise(n3, 78), I.neq_noise(n3, 79)
+
+    def shift(a):
+        return np.roll(a.reshape(-1, nz, ny, nx), (1, 2, 3), axis=(1, 2, 3)).reshape(a.shape)
+
+    def run(r, v, q, a, b):
+        p = O.lattice_params(nx, ny, nz, 27, 19, "edm", 0.55, 0.6, 3e-3, -2e-3)
+        s = O.OracleSim(p)
+        s.init_fields(r, v, q, a, b, 1e-3)
+        s.step(3)
+        return s.fields()
+
+    a = run(rho, u, rp, xf, xg)
+    b = run(shift(rho), shift(u), shift(rp), shift(xf), shift(xg))
+    for x, y in zip(a, b):
+        assert np.array_equal(shift(x), y)
+
+
+def test_power_of_two_rescaling_is_exact():
+    """g is linear: (G, beta, rho0) -> (G/4, 4 beta, 4 rho0) scales g, S and rho'
+    by 4 and leaves F = -G rho' and hence u bit-for-bit unchanged."""
+    outs = []
+    for lam in (1.0, 4.0):
+        p = O.lattice_params(5, 4, 6, 27, 19, "guo", 0.55, 0.6, 3e-3 / lam, -2e-3 * lam,
+                             rho0=lam)
+        s = O.OracleSim(p)
+        rho, u, rp = I.random_fields(5, 4, 6, 31, 0.05, 0.01, 0.5)
+        s.init_fields(rho, u, rp * lam)
+        s.step(5)
+        outs.append(s.fields())
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][2] * 4.0, outs[1][2])
+
+
+def test_energy_budget_laminar_tgv():
+    """Energy balance of Eqs. 2 and 4: -dE_tot/dt = eps_k + eps_p. In the laminar
+    stage of the 32^3 stratified TGV, the central time difference of E_k + E_p
+    matches the non-equilibrium eps_k plus eps_p within 3%."""
+    n, U0 = 32, 0.04
+    p = O.params_from_physics(n, 27, 19, "guo", 100.0, 0.5, 1.0, U0)
+    s = O.OracleSim(p)
+    s.init_fields(*I.tgv_fields(n, U0))
+    s.step(300)
+    dt = 20
+    e = []
+    for _ in range(3):
+        d = s.diagnostics()
+        e.append(d)
+        s.step(dt)
+    etot = [x["Ek"] + x["Ep"] for x in e]
+    rate = -(etot[2] - etot[0]) / (2 * dt)
+    eps = e[1]["eps_k"] + e[1]["eps_p"]
+    assert abs(rate / eps - 1) < 0.03, (rate, eps)
