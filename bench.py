@@ -1,0 +1,355 @@
+"""Throughput of the fused DDF stream-and-collide update on the stratified
+Taylor-Green vortex, in MLUPS (million lattice-node updates per second) and as
+a fraction of the measured HBM roofline.
+
+Workload: 256^3 periodic box, D3Q27 momentum x D3Q19 scalar stencils,
+Shan-Chen velocity-shift forcing, Re 800, Fr 0.1, Pr (= Sc) 1, U0 = 0.04,
+diagnostics (E_k, E_p, eps_k, eps_p) every 100 steps. One bench step is one
+diagnostics interval: 100 lattice updates plus one diagnostics evaluation.
+`value` is FP32-storage MLUPS over the timed steps; FP16/BF16 deviation
+storage (FP32 arithmetic) is timed the same way and reported beside it with
+its KE/PE/eps deviation from the FP32 run.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) each rank advances its own replica of the lattice
+(replicas only: the single-lattice workload has no data-parallel split
+without a halo exchange); `value` sums the ranks' node updates over the max
+per-rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 256
+PAIR = "27x19"
+FORCING = "sc"
+RE, FR, PR, U0 = 800.0, 0.1, 1.0, 0.04
+DIAG_EVERY = 100
+METRIC = "DDF MLUPS (FP32 storage) & % of HBM roofline; FP16-storage vs FP32 at <=1% KE/PE/eps error"
+WORKLOAD = "stratified TGV 256^3, D3Q27xD3Q19, velocity-shift (Shan-Chen) forcing, Re 800, Fr 0.1, Pr 1, U0 0.04"
+
+
+def bytes_per_node(storage: str) -> int:
+    # every population read once and written once per update
+    return (27 + 19) * 2 * (4 if storage == "fp32" else 2)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_gpu_arm(args):
+    import numpy as np
+    import torch
+
+    import stgv_inputs as inputs
+    from paper_2605_14505_gb300 import lbm
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    n3 = N ** 3
+    peak, peak_kind = measured_peaks()
+
+    def make(storage):
+        p = lbm.lbm_params_from_physics(N, N, N, PAIR, FORCING, RE, FR, PR, U0)
+        sim = lbm.Simulation(p, storage=storage)
+        sim.init_tgv(seed=1, noise_amp=1e-3)
+        return sim
+
+    def timed(sim, steps, warmup):
+        """Returns (seconds for `steps` bench steps, mean step-kernel launch ms, last diag)."""
+        stream = torch.cuda.ExternalStream(sim.stream.cuda_stream)
+        for _ in range(warmup):
+            sim.step(DIAG_EVERY)
+            sim.diagnostics()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        sim.synchronize()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        d = None
+        for k in range(steps):
+            ev[k][0].record(stream)
+            sim.step(DIAG_EVERY)
+            ev[k][1].record(stream)
+            d = sim.diagnostics()
+            ev[k][2].record(stream)
+        t1.record(stream)
+        sim.synchronize()
+        torch.cuda.synchronize()
+        barrier(world)
+        total_ms = t0.elapsed_time(t1)
+        step_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / (steps * DIAG_EVERY)
+        diag_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / steps
+        return total_ms / 1e3, step_ms, diag_ms, d
+
+    clocks = ClockSampler(local)
+    sim = make("fp32")
+    bx, by = lbm.lbm_get_block(sim.h)
+    clocks.start()
+    secs, step_ms, diag_ms, d32 = timed(sim, args.steps, args.warmup)
+    clk = clocks.stop()
+    secs = max_over_ranks(world, secs)
+    updates = float(n3) * DIAG_EVERY * args.steps * world
+    value = updates / secs / 1e6
+    achieved = bytes_per_node("fp32") * n3 / (step_ms * 1e-3) / 1e9
+    sim.close()
+
+    variants = {}
+    for storage in ("fp16", "bf16"):
+        s = make(storage)
+        vsecs, vstep_ms, _, dv = timed(s, args.steps, args.warmup)
+        vsecs = max_over_ranks(world, vsecs)
+        vmlups = float(n3) * DIAG_EVERY * args.steps * world / vsecs / 1e6
+        vach = bytes_per_node(storage) * n3 / (vstep_ms * 1e-3) / 1e9
+        err = {k: abs(dv[k] - d32[k]) / abs(d32[k]) for k in ("Ek", "Ep", "eps_k", "eps_p")}
+        variants[storage] = {
+            "mlups": round(vmlups, 1), "speedup_vs_fp32": round(vmlups / value, 3),
+            "step_kernel_ms": round(vstep_ms, 4),
+            "roofline": {"bound": "hbm", "achieved": round(vach, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(vach / peak, 4)},
+            "rel_dev_vs_fp32_gpu": {k: float(f"{v:.3e}") for k, v in err.items()},
+            "bytes_per_node": bytes_per_node(storage),
+        }
+        s.close()
+
+    # end to end through the C ABI with host buffers: per bench step, copy the
+    # initial fields from pinned host memory, advance 100 steps, read the
+    # diagnostics record back.
+    rho, u, rp = inputs.tgv_fields(N, U0, seed=1, noise_amp=1e-3)
+    hr = torch.from_numpy(rho).pin_memory()
+    hu = torch.from_numpy(np.ascontiguousarray(u)).pin_memory()
+    hp = torch.from_numpy(rp).pin_memory()
+    p = lbm.lbm_params_from_physics(N, N, N, PAIR, FORCING, RE, FR, PR, U0)
+    h = lbm.lbm_create_params(p)
+    dp = ctypes.POINTER(ctypes.c_double)
+    L = lbm.load_library()
+    ptrs = [ctypes.cast(t.data_ptr(), dp) for t in (hr, hu, hp)]
+
+    def e2e_step():
+        lbm._check(L.lbm_init_fields(h, ptrs[0], ptrs[1], ptrs[2], None, None, 0.0))
+        lbm.lbm_step(h, DIAG_EVERY)
+        return lbm.lbm_diagnostics(h)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    lbm.lbm_synchronize(h)
+    barrier(world)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    lbm.lbm_synchronize(h)
+    barrier(world)
+    e2e_secs = max_over_ranks(world, time.perf_counter() - t)
+    lbm.lbm_destroy(h)
+    e2e = {"value": round(float(n3) * DIAG_EVERY * args.steps * world / e2e_secs / 1e6, 1),
+           "unit": "MLUPS", "h2d_bytes_per_step": 5 * n3 * 8, "d2h_bytes_per_step": 11 * 8}
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs * 1e3 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (Eq. 20 Taylor-Green field + 1e-3 U0 SplitMix64 noise)",
+        "config": {"workload": WORKLOAD, "lattice": [N, N, N], "pair": "D3Q27xD3Q19", "forcing": "shan_chen",
+                   "storage": "fp32", "updates_per_step": DIAG_EVERY, "diagnostics_per_step": 1,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (3.09 GB store vs 129 MB L2)", "block": [bx, by]},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "kernel": "k_step<27x19, SC, f32> (even/odd AA)", "peak_kind": peak_kind,
+                     "bytes_per_node": bytes_per_node("fp32"), "step_kernel_ms": round(step_ms, 4),
+                     "diag_ms": round(diag_ms, 4)},
+        "storage_variants": variants,
+        "e2e": e2e,
+        "gpu_launches": args.steps * (DIAG_EVERY + 3),
+        "clocks": clk,
+    }
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def cpu_baseline(steps: int = 2) -> dict:
+    """The FP64 oracle as it stands on this host's cores: `steps` time steps of
+    the same 256^3 lattice (initialisation not timed)."""
+    import stgv_inputs as inputs
+    from oracle import oracle
+
+    p = oracle.params_from_physics(N, 27, 19, FORCING, RE, FR, PR, U0)
+    sim = oracle.OracleSim(p)
+    sim.init_fields(*inputs.tgv_fields(N, U0, seed=1, noise_amp=1e-3))
+    t = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t
+    sim.close()
+    return {"value": round(N ** 3 * steps / dt / 1e6, 3), "unit": "MLUPS", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{steps} time steps of the full {N}^3 lattice, FP64, "
+                                        "two-lattice pull streaming (init not timed)"}
+
+
+def run_reference_arm(args):
+    """The FP64 CPU oracle timed on the host cores on the same workload; each
+    bench step is one time step of the 256^3 lattice (a bounded sample of the
+    100-update diagnostics interval)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import stgv_inputs as inputs
+    from oracle import oracle
+
+    p = oracle.params_from_physics(N, 27, 19, FORCING, RE, FR, PR, U0)
+    sim = oracle.OracleSim(p)
+    sim.init_fields(*inputs.tgv_fields(N, U0, seed=1, noise_amp=1e-3))
+    sim.step(args.warmup)
+    t = time.perf_counter()
+    sim.step(args.steps)
+    dt = time.perf_counter() - t
+    sim.close()
+    value = N ** 3 * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (Eq. 20 Taylor-Green field + 1e-3 U0 SplitMix64 noise)",
+        "config": {"workload": WORKLOAD, "lattice": [N, N, N], "pair": "D3Q27xD3Q19", "forcing": "shan_chen",
+                   "storage": "fp64", "updates_per_step": 1, "parallelism": "host cores"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"{args.steps} time steps of the full {N}^3 lattice per run, FP64"},
+        "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference_arm(args)
+    else:
+        run_gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) double-distribution-function lattice
+ * Boltzmann solver for the Boussinesq stratified Taylor-Green vortex.
+ *
+ * The operation behind this interface is the fused stream-and-collide update
+ * of the paper's Section 2: momentum populations f_i on D3Q27 or D3Q19
+ * (Eqs. 5-10), scalar populations g_i for the density perturbation rho' on
+ * D3Q19 or D3Q7 (Eqs. 11-17), BGK relaxation (Eqs. 8, 14), the buoyancy force
+ * F = (0, 0, -G rho') (Eq. 18) applied by the Guo source term, the Shan-Chen
+ * velocity shift (Eq. 10), the exact difference method or the HCZ source term
+ * (Section 3.6), the stencils of Table A.1, the Taylor-Green initial state of
+ * Eq. 20 (Section 2.4) and the energy / dissipation diagnostics of Eqs. 22-26.
+ *
+ * Conventions.
+ *  - Every function returns an int status: LBM_OK (0) or a negative LBM_E*
+ *    code. On error, lbm_last_error() returns a message for the calling thread
+ *    and the handle is left unchanged unless stated otherwise.
+ *  - Lattice units throughout. Node (x, y, z) has linear index
+ *    x + nx * (y + ny * z); host arrays are FP64, x fastest. A vector field is
+ *    three consecutive blocks of nx*ny*nz values (u_x, then u_y, then u_z).
+ *  - Populations per node are indexed in this library's slot order (see
+ *    lbm_velocity_set): rest, 6 axis directions, 12 edges, 8 corners, with
+ *    slots 2m-1 and 2m opposite.
+ *  - Device work is enqueued on the handle's CUDA stream. lbm_step returns
+ *    without waiting; functions that return host data wait for the stream.
+ *  - Handles are opaque and owned by the library (lbm_destroy frees them).
+ *    A handle is not thread-safe: one thread at a time.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LBM_OK 0
+#define LBM_EINVAL (-1)        /* invalid argument */
+#define LBM_ENOMEM (-2)        /* device or host allocation failed */
+#define LBM_ECUDA (-3)         /* CUDA runtime error (message has the CUDA error string) */
+#define LBM_ETIMEOUT (-4)      /* a bounded device wait ran out */
+#define LBM_ENONFINITE (-5)    /* diagnostics found NaN or Inf (output still filled) */
+#define LBM_EUNSUPPORTED (-6)  /* combination not compiled into this library */
+#define LBM_ESTATE (-7)        /* call out of order (e.g. step before init) */
+
+/* stencil pairs D3Q(m) x D3Q(n): m for f, n for g (Section 2.3) */
+enum lbm_pair {
+    LBM_D3Q27_D3Q19 = 0,
+    LBM_D3Q19_D3Q7 = 1,
+    LBM_D3Q27_D3Q27 = 2,
+    LBM_D3Q19_D3Q19 = 3,
+    LBM_D3Q19_D3Q15 = 4,
+    LBM_D3Q15_D3Q7 = 5,
+    LBM_D3Q7_D3Q27 = 6
+};
+
+/* forcing schemes (Section 3.6) */
+enum lbm_forcing {
+    LBM_GUO = 0,        /* Guo-Zheng-Shi discrete source term, u of Eq. 7 */
+    LBM_SHAN_CHEN = 1,  /* velocity shift, Eq. 10 */
+    LBM_EDM = 2,        /* exact difference method */
+    LBM_HCZ = 3         /* He-Chen-Zhang source term */
+};
+
+/* population storage in HBM: FP32, or FP16/BF16 deviations f_i - w_i
+ * (g_i - w_i rho0); the collision arithmetic is FP32 in every case */
+enum lbm_storage { LBM_FP32 = 0, LBM_FP16_DEV = 1, LBM_BF16_DEV = 2 };
+
+/* scalar source/moment pair (Eqs. 11, 16, 17) */
+enum lbm_scalar_mode {
+    LBM_SCALAR_PRINTED = 0,  /* LBE adds S_i, rho' = sum g + (1/2) sum R_i - rho0 (as printed) */
+    LBM_SCALAR_CHAI_SHI = 1  /* LBE adds R_i, rho' = sum g + (1/2) sum S_i - rho0 */
+};
+
+/* Lattice-unit parameters. lbm_params_from_physics fills them from the
+ * dimensionless numbers of Section 2.4. */
+typedef struct lbm_params {
+    int32_t nx, ny, nz;      /* lattice size, each >= 1, periodic */
+    int32_t pair;            /* enum lbm_pair */
+    int32_t forcing;         /* enum lbm_forcing */
+    int32_t storage;         /* enum lbm_storage */
+    int32_t scalar_mode;     /* enum lbm_scalar_mode */
+    int32_t reserved;
+    double tau_f;            /* Eq. 8: nu / cs^2 + 1/2, > 1/2 */
+    double tau_g;            /* Eq. 14: D / cs^2 + 1/2, > 1/2 */
+    double G;                /* gravity in lattice units (Eq. 18) */
+    double beta;             /* (d rho_b / dz)_LU (Eqs. 12, 13) */
+    double rho0;             /* reference density (Eqs. 3, 15) */
+    double sc_shift;         /* Shan-Chen shift u_eq = j/rho + sc_shift tau_f F/rho;
+                                1 standard, 0.5 = Eq. 10 as printed */
+    double U0;               /* reference velocity, lattice units (reporting only) */
+    double L;                /* reference length L = 1 in lattice spacings (reporting only) */
+} lbm_params;
+
+/* Diagnostics of the current state (post-stream, pre-collision), lattice
+ * units, averages over all nodes (Eqs. 22-26). */
+typedef struct lbm_diag {
+    double Ek;          /* <|u|^2 / 2>, u of Eq. 7 (Eq. 22) */
+    double Ep;          /* <(G/N)^2 (rho'/rho0)^2 / 2> (Eq. 23) */
+    double eps_k;       /* 2 nu <S:S>, S from the non-equilibrium second moment of f */
+    double eps_p;       /* D <(G/N)^2 |grad rho'|^2 / rho0^2>, central differences (Eq. 26) */
+    double eps_k_curl;  /* nu <|curl u|^2>, central differences (Eq. 25) */
+    double mass_f;      /* sum over nodes and slots of f_i */
+    double mass_g;      /* sum over nodes and slots of g_i */
+    double mom[3];      /* sum over nodes and slots of e_i f_i */
+    double umax;        /* max |u| */
+    int64_t step;       /* time steps taken since initialisation */
+} lbm_diag;
+
+typedef struct lbm_ctx* lbm_handle;
+
+/* Message of the last failed call on this thread ("" if none). Never NULL. */
+const char* lbm_last_error(void);
+
+/* Library version string. */
+const char* lbm_version(void);
+
+/* Velocity set q in {7, 15, 19, 27} in this library's slot order:
+ * e[3*i + a] (a = x, y, z), w[i] (Table A.1), *cs2. Arrays of 27 suffice.
+ * Returns q, or LBM_EINVAL for another q. Any pointer may be NULL. */
+int lbm_velocity_set(int q, int* e, double* w, double* cs2);
+
+/* Section 2.4 and Eq. 19 -> lattice units for an n^3 box [0, 2 pi)^3
+ * (n = nx; ny and nz are copied): L = nx / (2 pi), nu = U0 L / Re,
+ * D = nu / Pr (Pr is the paper's Schmidt number Sc), tau_f = nu / cs^2 + 1/2,
+ * tau_g = D / cs_g^2 + 1/2, N = U0 / (Fr L) (Fr may be +inf: unstratified),
+ * rho0 = 1, G = N / 1024 and beta = -N^2 rho0 / G (Eq. 19 fixes only their
+ * product), storage FP32, printed scalar pair, standard Shan-Chen shift.
+ * Returns LBM_EINVAL for non-positive Re, Pr, U0, Fr or sizes. */
+int lbm_params_from_physics(lbm_params* p, int nx, int ny, int nz, int pair, int forcing,
+                            double Re, double Fr, double Pr, double U0);
+
+/* Create a simulation from physical numbers (= lbm_params_from_physics +
+ * lbm_create_params). The current CUDA device becomes the handle's device.
+ * No device memory is allocated until lbm_attach or the first init call. */
+int lbm_create(lbm_handle* out, int nx, int ny, int nz, int pair, int forcing,
+               double Re, double Fr, double Pr, double U0);
+
+/* Create a simulation from lattice-unit parameters (copied). LBM_EUNSUPPORTED
+ * if the (pair, storage) kernels are not compiled into this library. */
+int lbm_create_params(lbm_handle* out, const lbm_params* p);
+
+/* Copy the handle's parameters out. */
+int lbm_get_params(lbm_handle h, lbm_params* p);
+
+/* Change the storage type (enum lbm_storage). Only before the first init
+ * call or lbm_attach (LBM_ESTATE afterwards). */
+int lbm_set_storage(lbm_handle h, int storage);
+
+/* Enqueue all later device work on this cudaStream_t (not owned; NULL = the
+ * legacy default stream, which also disables CUDA-graph replay). */
+int lbm_set_stream(lbm_handle h, void* stream);
+
+/* Bytes of the population store: (Q_f + Q_g) * nx*ny*nz * element size. */
+int lbm_required_bytes(lbm_handle h, size_t* bytes);
+
+/* Use caller-owned device memory (>= lbm_required_bytes, 256-byte aligned,
+ * on the handle's device) as the population store; the caller keeps
+ * ownership and must keep it alive until lbm_destroy. Must precede init. */
+int lbm_attach(lbm_handle h, void* device_ptr, size_t bytes);
+
+/* Eq. 20 initial state (Section 2.4): u = U0 (sin x cos y cos z,
+ * -cos x sin y cos z, 0) on x_i = 2 pi i / n, rho = 1, rho' = 0, plus
+ * noise_amp * U0 * xi per component with xi uniform in [-1, 1) drawn from
+ * SplitMix64(seed) at counter c = component * nx*ny*nz + node. Populations
+ * are set to the equilibria f_eq(rho, u) (Eq. 9), g_eq(rho', u) (Eq. 15).
+ * Requires nx = ny = nz (LBM_EINVAL otherwise). Resets the step counter. */
+int lbm_init_tgv(lbm_handle h, uint64_t seed, double noise_amp);
+
+/* Populations from host FP64 fields (not retained): rho[n3], u[3*n3],
+ * rho_p[n3]; f = f_eq(rho, u) + amp w_i xi_f[code(e_i)][node],
+ * g = g_eq(rho', u) + amp w_i xi_g[code(e_i)][node], where the optional
+ * xi_f, xi_g are [27][n3] arrays indexed by code(e) = (ex+1)*9 + (ey+1)*3 +
+ * (ez+1) (NULL: no perturbation). Waits for completion. Resets the step counter. */
+int lbm_init_fields(lbm_handle h, const double* rho, const double* u, const double* rho_p,
+                    const double* xi_f, const double* xi_g, double amp);
+
+/* Advance nsteps >= 0 time steps (Eqs. 5, 11: collide, then stream) with
+ * the in-place AA pattern; asynchronous on the handle's stream. */
+int lbm_step(lbm_handle h, int64_t nsteps);
+
+/* Block until the handle's stream is idle; reports asynchronous CUDA errors. */
+int lbm_synchronize(lbm_handle h);
+
+/* Diagnostics of the current state into *out (waits for the stream).
+ * LBM_ENONFINITE if any value is NaN/Inf (out is still written). */
+int lbm_diagnostics(lbm_handle h, lbm_diag* out);
+
+/* Macroscopic fields of the current state into host FP64 arrays: rho (Eq. 6),
+ * physical u (Eq. 7, 3 blocks), rho' (Eq. 16). Any pointer may be NULL. */
+int lbm_get_fields(lbm_handle h, double* rho, double* u, double* rho_p);
+
+/* Full populations (not deviations) of the current state in FP64, host
+ * arrays f[Q_f][n3], g[Q_g][n3], slot order of lbm_velocity_set. */
+int lbm_get_populations(lbm_handle h, double* f, double* g);
+
+/* Full populations (FP64) of `count` sampled nodes of the current state:
+ * nodes[k] is a linear node index (< nx*ny*nz, else LBM_EINVAL); outputs are
+ * f[k * Q_f + i], g[k * Q_g + i] in this library's slot order. For
+ * spot checks of large lattices without copying the whole store. */
+int lbm_sample_populations(lbm_handle h, const int64_t* nodes, int64_t count, double* f, double* g);
+
+/* Overwrite the populations from host FP64 arrays laid out as in
+ * lbm_get_populations (checkpoint restore). The step counter is kept. */
+int lbm_set_populations(lbm_handle h, const double* f, const double* g);
+
+/* Time steps taken since the last init. */
+int lbm_step_count(lbm_handle h, int64_t* step);
+
+/* Launch shape of the step kernel (threads along x and y; bx * by <= 256,
+ * bx a multiple of 32). */
+int lbm_set_block(lbm_handle h, int bx, int by);
+int lbm_get_block(lbm_handle h, int* bx, int* by);
+
+/* Time each candidate launch shape on this lattice (reps even+odd step pairs
+ * each, CUDA events) and keep the fastest. The state is saved and restored,
+ * so the simulation is unchanged. best_ms_per_step may be NULL. */
+int lbm_autotune(lbm_handle h, int reps, double* best_ms_per_step);
+
+/* Enable (1, default) or disable (0) CUDA-graph replay in lbm_step. */
+int lbm_set_graphs(lbm_handle h, int enable);
+
+/* Free the handle and every library-owned device buffer. NULL is allowed. */
+int lbm_destroy(lbm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,814 @@
+// C ABI (include/lbm.h): handle management, parameter mapping, launches,
+// CUDA-graph replay of the AA step pair, diagnostics, autotuning.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_dispatch.h"
+#include "lbm_kernels.cuh"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(call, what)                                   \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);     \
+    } while (0)
+
+struct PairInfo {
+    int qf, qg;
+};
+
+bool pair_info(int pair, PairInfo* out)
+{
+    static const PairInfo t[7] = {{27, 19}, {19, 7}, {27, 27}, {19, 19}, {19, 15}, {15, 7}, {7, 27}};
+    if (pair < 0 || pair > 6) return false;
+    *out = t[pair];
+    return true;
+}
+
+double cs2_of(int q) { return q == 7 ? 0.25 : 1.0 / 3.0; }
+
+size_t elem_size(int storage) { return storage == LBM_FP32 ? 4 : 2; }
+
+constexpr int kGraphSteps = 64;   // even number: the graph starts and ends in natural layout
+
+}  // namespace
+
+struct lbm_ctx {
+    lbm_params p{};
+    PairInfo q{};
+    Geometry geo{};
+    Phys ph{};
+    const KernelSet* ks = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void* store = nullptr;
+    size_t store_bytes = 0;
+    bool own_store = false;
+    bool initialized = false;
+    int64_t step = 0;
+    int odd = 0;           // layout parity of the store
+    int bx = 0, by = 0;
+    // diagnostics scratch
+    float* diag_fields = nullptr;
+    double* diag_partials = nullptr;
+    double* diag_out = nullptr;
+    double* diag_host = nullptr;   // pinned
+    int diag_blocks = 0;
+    // host<->device staging
+    double* staging = nullptr;
+    size_t staging_bytes = 0;
+    // CUDA graph of kGraphSteps steps starting from the natural layout
+    bool graphs = true;
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t graph_stream = nullptr;
+};
+
+namespace {
+
+void derive_phys(lbm_ctx* h)
+{
+    const lbm_params& p = h->p;
+    Phys& ph = h->ph;
+    ph.omega_f = (float)(1.0 / p.tau_f);
+    ph.omega_g = (float)(1.0 / p.tau_g);
+    ph.G = (float)p.G;
+    ph.beta = (float)p.beta;
+    ph.rho0 = (float)p.rho0;
+    const double c_mom = (p.scalar_mode == LBM_SCALAR_PRINTED) ? 0.5 * (1.0 - 1.0 / (2.0 * p.tau_g)) : 0.5;
+    const double c_lbe = (p.scalar_mode == LBM_SCALAR_PRINTED) ? 1.0 : 1.0 - 1.0 / (2.0 * p.tau_g);
+    ph.kappa = (float)(c_mom * -p.beta);
+    ph.c_lbe = (float)c_lbe;
+    ph.guo_pref = (float)(1.0 - 1.0 / (2.0 * p.tau_f));
+    ph.sc_tau = (float)(p.sc_shift * p.tau_f);
+    h->geo.nx = p.nx;
+    h->geo.ny = p.ny;
+    h->geo.nz = p.nz;
+    h->geo.n3 = (uint32_t)((size_t)p.nx * p.ny * p.nz);
+}
+
+void default_block(lbm_ctx* h)
+{
+    int bx = h->p.nx >= 128 ? 128 : (h->p.nx >= 64 ? 64 : 32);
+    int by = 256 / bx;
+    while (by > 1 && by / 2 >= h->p.ny) by /= 2;
+    h->bx = bx;
+    h->by = by;
+}
+
+void drop_graph(lbm_ctx* h)
+{
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+}
+
+int ensure_store(lbm_ctx* h)
+{
+    if (h->store) return LBM_OK;
+    size_t bytes = (size_t)(h->q.qf + h->q.qg) * h->geo.n3 * elem_size(h->p.storage);
+    void* ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ENOMEM, "cudaMalloc of %zu bytes for the population store failed: %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    h->store = ptr;
+    h->store_bytes = bytes;
+    h->own_store = true;
+    return LBM_OK;
+}
+
+void* f_ptr(lbm_ctx* h) { return h->store; }
+void* g_ptr(lbm_ctx* h)
+{
+    return static_cast<char*>(h->store) + (size_t)h->q.qf * h->geo.n3 * elem_size(h->p.storage);
+}
+
+int ensure_staging(lbm_ctx* h, size_t bytes)
+{
+    if (h->staging_bytes >= bytes) return LBM_OK;
+    if (h->staging) cudaFree(h->staging);
+    h->staging = nullptr;
+    h->staging_bytes = 0;
+    cudaError_t e = cudaMalloc(&h->staging, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->staging = nullptr;
+        return fail(LBM_ENOMEM, "cudaMalloc of %zu staging bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    h->staging_bytes = bytes;
+    return LBM_OK;
+}
+
+int ensure_diag(lbm_ctx* h)
+{
+    if (h->diag_fields) return LBM_OK;
+    h->diag_blocks = 4 * (h->num_sms > 0 ? h->num_sms : 132);
+    size_t fbytes = 4 * (size_t)h->geo.n3 * sizeof(float);
+    if (cudaMalloc(&h->diag_fields, fbytes) != cudaSuccess ||
+        cudaMalloc(&h->diag_partials, (size_t)h->diag_blocks * kDNumSlots * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h->diag_out, 16 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&h->diag_host, 16 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ENOMEM, "diagnostics scratch allocation failed");
+    }
+    return LBM_OK;
+}
+
+dim3 step_grid(const lbm_ctx* h)
+{
+    return dim3((unsigned)((h->p.nx + h->bx - 1) / h->bx), (unsigned)((h->p.ny + h->by - 1) / h->by),
+                (unsigned)h->p.nz);
+}
+
+cudaError_t launch_step(lbm_ctx* h, int odd, cudaStream_t s)
+{
+    StepArgs a;
+    a.f = f_ptr(h);
+    a.g = g_ptr(h);
+    a.geo = h->geo;
+    a.ph = h->ph;
+    void* args[] = {&a};
+    return cudaLaunchKernel(h->ks->step[h->p.forcing][odd], step_grid(h), dim3(h->bx, h->by), args, 0, s);
+}
+
+int flat_grid(const lbm_ctx* h)
+{
+    size_t blocks = ((size_t)h->geo.n3 + 255) / 256;
+    size_t cap = (size_t)(h->num_sms > 0 ? h->num_sms : 132) * 16;
+    return (int)(blocks < cap ? blocks : cap);
+}
+
+int check_handle(lbm_ctx* h)
+{
+    if (!h) return fail(LBM_EINVAL, "null handle");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return LBM_OK;
+}
+
+int validate_params(const lbm_params* p, PairInfo* q)
+{
+    if (!p) return fail(LBM_EINVAL, "null parameters");
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(LBM_EINVAL, "lattice sizes must be >= 1");
+    size_t n3 = (size_t)p->nx * p->ny * p->nz;
+    if (n3 > 0x7fffffffull) return fail(LBM_EINVAL, "nx*ny*nz = %zu exceeds 2^31 - 1 nodes", n3);
+    if (p->nz > 65535) return fail(LBM_EINVAL, "nz must be <= 65535");
+    if (!pair_info(p->pair, q)) return fail(LBM_EINVAL, "unknown stencil pair %d", p->pair);
+    if ((size_t)(q->qf > q->qg ? q->qf : q->qg) * n3 > 0xffffffffull)
+        return fail(LBM_EINVAL, "Q * nx*ny*nz = %zu exceeds the 32-bit element offsets of the store",
+                    (size_t)(q->qf > q->qg ? q->qf : q->qg) * n3);
+    if (p->forcing < 0 || p->forcing > 3) return fail(LBM_EINVAL, "unknown forcing scheme %d", p->forcing);
+    if (p->storage < 0 || p->storage > 2) return fail(LBM_EINVAL, "unknown storage %d", p->storage);
+    if (p->scalar_mode < 0 || p->scalar_mode > 1) return fail(LBM_EINVAL, "unknown scalar mode %d", p->scalar_mode);
+    if (!(p->tau_f > 0.5) || !(p->tau_g > 0.5) || !std::isfinite(p->tau_f) || !std::isfinite(p->tau_g))
+        return fail(LBM_EINVAL, "relaxation times must be finite and > 1/2 (tau_f=%g, tau_g=%g)", p->tau_f,
+                    p->tau_g);
+    if (!std::isfinite(p->G) || !std::isfinite(p->beta) || !std::isfinite(p->rho0) || !std::isfinite(p->sc_shift))
+        return fail(LBM_EINVAL, "non-finite physical parameter");
+    return LBM_OK;
+}
+
+int after_init(lbm_ctx* h)
+{
+    h->initialized = true;
+    h->step = 0;
+    h->odd = 0;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_last_error(void) { return g_last_error.c_str(); }
+
+const char* lbm_version(void) { return "paper_2605_14505_gb300 lbm 0.1 (sm_103a)"; }
+
+int lbm_velocity_set(int q, int* e, double* w, double* cs2)
+{
+    auto fill = [&](auto lat) {
+        using L = decltype(lat);
+        for (int i = 0; i < L::kQ; ++i) {
+            if (e) {
+                e[3 * i + 0] = L::ex(i);
+                e[3 * i + 1] = L::ey(i);
+                e[3 * i + 2] = L::ez(i);
+            }
+            if (w) w[i] = L::wd(i);
+        }
+        if (cs2) *cs2 = L::cs2d;
+        return L::kQ;
+    };
+    switch (q) {
+    case 7: return fill(Lattice<7>{});
+    case 15: return fill(Lattice<15>{});
+    case 19: return fill(Lattice<19>{});
+    case 27: return fill(Lattice<27>{});
+    default: return fail(LBM_EINVAL, "unknown velocity set Q%d", q);
+    }
+}
+
+int lbm_params_from_physics(lbm_params* p, int nx, int ny, int nz, int pair, int forcing, double Re,
+                            double Fr, double Pr, double U0)
+{
+    PairInfo q;
+    if (!p) return fail(LBM_EINVAL, "null parameters");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(LBM_EINVAL, "lattice sizes must be >= 1");
+    if (!pair_info(pair, &q)) return fail(LBM_EINVAL, "unknown stencil pair %d", pair);
+    if (!(Re > 0) || !(Pr > 0) || !(U0 > 0) || !(Fr > 0) || std::isnan(Fr))
+        return fail(LBM_EINVAL, "Re, Fr, Pr and U0 must be positive");
+    std::memset(p, 0, sizeof(*p));
+    const double two_pi = 6.283185307179586476925286766559;
+    const double L = nx / two_pi;
+    const double nu = U0 * L / Re;
+    const double D = nu / Pr;
+    const double N = std::isinf(Fr) ? 0.0 : U0 / (Fr * L);
+    p->nx = nx;
+    p->ny = ny;
+    p->nz = nz;
+    p->pair = pair;
+    p->forcing = forcing;
+    p->storage = LBM_FP32;
+    p->scalar_mode = LBM_SCALAR_PRINTED;
+    p->tau_f = nu / cs2_of(q.qf) + 0.5;
+    p->tau_g = D / cs2_of(q.qg) + 0.5;
+    p->rho0 = 1.0;
+    p->G = N / 1024.0;
+    p->beta = N > 0 ? -N * N * p->rho0 / p->G : 0.0;
+    p->sc_shift = 1.0;
+    p->U0 = U0;
+    p->L = L;
+    return LBM_OK;
+}
+
+int lbm_create_params(lbm_handle* out, const lbm_params* p)
+{
+    if (!out) return fail(LBM_EINVAL, "null output handle");
+    *out = nullptr;
+    PairInfo q;
+    int rc = validate_params(p, &q);
+    if (rc) return rc;
+    const KernelSet* ks = kernel_set(p->pair, p->storage);
+    if (!ks) return fail(LBM_EUNSUPPORTED, "stencil pair %d with storage %d is not compiled in", p->pair, p->storage);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    lbm_ctx* h = new (std::nothrow) lbm_ctx();
+    if (!h) return fail(LBM_ENOMEM, "host allocation failed");
+    h->p = *p;
+    h->q = q;
+    h->ks = ks;
+    h->device = dev;
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    derive_phys(h);
+    default_block(h);
+    e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    h->own_stream = true;
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_create(lbm_handle* out, int nx, int ny, int nz, int pair, int forcing, double Re, double Fr, double Pr,
+               double U0)
+{
+    lbm_params p;
+    int rc = lbm_params_from_physics(&p, nx, ny, nz, pair, forcing, Re, Fr, Pr, U0);
+    if (rc) return rc;
+    return lbm_create_params(out, &p);
+}
+
+int lbm_get_params(lbm_handle h, lbm_params* p)
+{
+    if (!h || !p) return fail(LBM_EINVAL, "null argument");
+    *p = h->p;
+    return LBM_OK;
+}
+
+int lbm_set_storage(lbm_handle h, int storage)
+{
+    if (!h) return fail(LBM_EINVAL, "null handle");
+    if (h->store) return fail(LBM_ESTATE, "storage can only change before the store exists");
+    if (storage < 0 || storage > 2) return fail(LBM_EINVAL, "unknown storage %d", storage);
+    const KernelSet* ks = kernel_set(h->p.pair, storage);
+    if (!ks) return fail(LBM_EUNSUPPORTED, "storage %d is not compiled in for pair %d", storage, h->p.pair);
+    h->p.storage = storage;
+    h->ks = ks;
+    drop_graph(h);
+    return LBM_OK;
+}
+
+int lbm_set_stream(lbm_handle h, void* stream)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (h->own_stream) {
+        cudaStreamSynchronize(h->stream);
+        cudaStreamDestroy(h->stream);
+    }
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->own_stream = false;
+    return LBM_OK;
+}
+
+int lbm_required_bytes(lbm_handle h, size_t* bytes)
+{
+    if (!h || !bytes) return fail(LBM_EINVAL, "null argument");
+    *bytes = (size_t)(h->q.qf + h->q.qg) * h->geo.n3 * elem_size(h->p.storage);
+    return LBM_OK;
+}
+
+int lbm_attach(lbm_handle h, void* device_ptr, size_t bytes)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (h->store) return fail(LBM_ESTATE, "a population store is already in place");
+    size_t need;
+    lbm_required_bytes(h, &need);
+    if (!device_ptr) return fail(LBM_EINVAL, "null device pointer");
+    if (bytes < need) return fail(LBM_EINVAL, "store of %zu bytes is smaller than the %zu required", bytes, need);
+    if (reinterpret_cast<uintptr_t>(device_ptr) % 256 != 0) return fail(LBM_EINVAL, "store must be 256-byte aligned");
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, device_ptr);
+    if (e != cudaSuccess || attr.type != cudaMemoryTypeDevice || attr.device != h->device) {
+        cudaGetLastError();
+        return fail(LBM_EINVAL, "store must be device memory on the handle's device");
+    }
+    h->store = device_ptr;
+    h->store_bytes = bytes;
+    h->own_store = false;
+    return LBM_OK;
+}
+
+int lbm_init_tgv(lbm_handle h, uint64_t seed, double noise_amp)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (h->p.nx != h->p.ny || h->p.nx != h->p.nz) return fail(LBM_EINVAL, "the Taylor-Green box needs nx = ny = nz");
+    if (!std::isfinite(noise_amp)) return fail(LBM_EINVAL, "non-finite noise amplitude");
+    if ((rc = ensure_store(h))) return rc;
+    drop_graph(h);
+    TgvArgs a;
+    a.f = f_ptr(h);
+    a.g = g_ptr(h);
+    a.geo = h->geo;
+    a.U0 = h->p.U0;
+    a.noise = noise_amp;
+    a.seed = seed;
+    a.rho0 = h->p.rho0;
+    void* args[] = {&a};
+    LBM_CUDA(cudaLaunchKernel(h->ks->init_tgv, dim3(flat_grid(h)), dim3(256), args, 0, h->stream), "init_tgv launch");
+    return after_init(h);
+}
+
+int lbm_init_fields(lbm_handle h, const double* rho, const double* u, const double* rho_p, const double* xi_f,
+                    const double* xi_g, double amp)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!rho || !u || !rho_p) return fail(LBM_EINVAL, "rho, u and rho_p are required");
+    if ((rc = ensure_store(h))) return rc;
+    const size_t n3 = h->geo.n3;
+    size_t ndoubles = 5 * n3 + (xi_f ? 27 * n3 : 0) + (xi_g ? 27 * n3 : 0);
+    if ((rc = ensure_staging(h, ndoubles * sizeof(double)))) return rc;
+    drop_graph(h);
+    double* d = h->staging;
+    LBM_CUDA(cudaMemcpyAsync(d, rho, n3 * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy rho");
+    LBM_CUDA(cudaMemcpyAsync(d + n3, u, 3 * n3 * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy u");
+    LBM_CUDA(cudaMemcpyAsync(d + 4 * n3, rho_p, n3 * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy rho_p");
+    double* dxf = nullptr;
+    double* dxg = nullptr;
+    size_t off = 5 * n3;
+    if (xi_f) {
+        dxf = d + off;
+        off += 27 * n3;
+        LBM_CUDA(cudaMemcpyAsync(dxf, xi_f, 27 * n3 * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy xi_f");
+    }
+    if (xi_g) {
+        dxg = d + off;
+        LBM_CUDA(cudaMemcpyAsync(dxg, xi_g, 27 * n3 * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy xi_g");
+    }
+    InitArgs a;
+    a.f = f_ptr(h);
+    a.g = g_ptr(h);
+    a.geo = h->geo;
+    a.rho = d;
+    a.u = d + n3;
+    a.rho_p = d + 4 * n3;
+    a.xi_f = dxf;
+    a.xi_g = dxg;
+    a.amp = amp;
+    a.rho0 = h->p.rho0;
+    void* args[] = {&a};
+    LBM_CUDA(cudaLaunchKernel(h->ks->init_fields, dim3(flat_grid(h)), dim3(256), args, 0, h->stream),
+             "init_fields launch");
+    LBM_CUDA(cudaStreamSynchronize(h->stream), "init_fields");
+    return after_init(h);
+}
+
+int lbm_step(lbm_handle h, int64_t nsteps)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (nsteps < 0) return fail(LBM_EINVAL, "negative step count");
+    if (!h->initialized) return fail(LBM_ESTATE, "lbm_step before initialisation");
+    while (nsteps > 0) {
+        if (h->graphs && h->stream != nullptr && h->odd == 0 && nsteps >= kGraphSteps) {
+            if (!h->graph) {
+                cudaGraph_t g = nullptr;
+                cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    for (int s = 0; s < kGraphSteps && e == cudaSuccess; ++s) e = launch_step(h, s & 1, h->stream);
+                    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+                    if (e == cudaSuccess) e = e2;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph, g, 0);
+                if (g) cudaGraphDestroy(g);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    h->graph = nullptr;
+                    h->graphs = false;  // fall back to eager launches
+                    continue;
+                }
+            }
+            LBM_CUDA(cudaGraphLaunch(h->graph, h->stream), "graph launch");
+            h->step += kGraphSteps;
+            nsteps -= kGraphSteps;
+            continue;
+        }
+        LBM_CUDA(launch_step(h, h->odd, h->stream), "step launch");
+        h->odd ^= 1;
+        h->step += 1;
+        nsteps -= 1;
+    }
+    return LBM_OK;
+}
+
+int lbm_synchronize(lbm_handle h)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    LBM_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    return LBM_OK;
+}
+
+int lbm_diagnostics(lbm_handle h, lbm_diag* out)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!out) return fail(LBM_EINVAL, "null output");
+    if (!h->initialized) return fail(LBM_ESTATE, "diagnostics before initialisation");
+    if ((rc = ensure_diag(h))) return rc;
+    const lbm_params& p = h->p;
+    const double cs2f = cs2_of(h->q.qf), cs2g = cs2_of(h->q.qg);
+    const double gn2 = (p.beta != 0.0) ? (-p.G * p.rho0 / p.beta) : 1.0;
+    const double nu = cs2f * (p.tau_f - 0.5), D = cs2g * (p.tau_g - 0.5);
+    DiagArgs a;
+    a.f = f_ptr(h);
+    a.g = g_ptr(h);
+    a.geo = h->geo;
+    a.ph = h->ph;
+    a.odd = h->odd;
+    a.ep_scale = (float)(0.5 * gn2 / (p.rho0 * p.rho0));
+    a.epsk_scale = (float)(2.0 * nu);
+    a.s_scale = (float)(-1.0 / (2.0 * cs2f * p.tau_f));
+    a.epsp_scale = (float)(D * gn2 / (p.rho0 * p.rho0));
+    a.nu = (float)nu;
+    a.fields = h->diag_fields;
+    a.partials = h->diag_partials;
+    void* args[] = {&a};
+    LBM_CUDA(cudaLaunchKernel(h->ks->diag_moments, dim3(h->diag_blocks), dim3(kDiagBlock), args, 0, h->stream),
+             "diag pass 1");
+    LBM_CUDA(cudaLaunchKernel(diag_gradients_kernel(), dim3(h->diag_blocks), dim3(kDiagBlock), args, 0, h->stream),
+             "diag pass 2");
+    const double* pp = h->diag_partials;
+    int nb = h->diag_blocks;
+    double* dout = h->diag_out;
+    void* fargs[] = {&pp, &nb, &dout};
+    LBM_CUDA(cudaLaunchKernel(diag_final_kernel(), dim3(1), dim3(kDiagBlock), fargs, 0, h->stream), "diag pass 3");
+    LBM_CUDA(cudaMemcpyAsync(h->diag_host, h->diag_out, kDNumSlots * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+             "diag copy");
+    LBM_CUDA(cudaStreamSynchronize(h->stream), "diagnostics");
+    const double* s = h->diag_host;
+    const double inv = 1.0 / (double)h->geo.n3;
+    out->Ek = s[kDEk] * inv;
+    out->Ep = s[kDEp] * inv;
+    out->eps_k = s[kDEpsK] * inv;
+    out->eps_p = s[kDEpsP] * inv;
+    out->eps_k_curl = s[kDEpsKCurl] * inv;
+    out->mass_f = (double)h->geo.n3 + s[kDDrho];
+    out->mass_g = (double)h->geo.n3 * p.rho0 + s[kDA];
+    out->mom[0] = s[kDJx];
+    out->mom[1] = s[kDJy];
+    out->mom[2] = s[kDJz];
+    out->umax = s[kDUmax];
+    out->step = h->step;
+    for (int q = 0; q < kDNumSlots; ++q)
+        if (!std::isfinite(s[q])) return fail(LBM_ENONFINITE, "non-finite diagnostics at step %lld", (long long)h->step);
+    return LBM_OK;
+}
+
+int lbm_get_fields(lbm_handle h, double* rho, double* u, double* rho_p)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!h->initialized) return fail(LBM_ESTATE, "fields requested before initialisation");
+    const size_t n3 = h->geo.n3;
+    if ((rc = ensure_staging(h, 5 * n3 * sizeof(double)))) return rc;
+    FieldArgs a;
+    a.f = f_ptr(h);
+    a.g = g_ptr(h);
+    a.geo = h->geo;
+    a.ph = h->ph;
+    a.odd = h->odd;
+    a.rho = h->staging;
+    a.u = h->staging + n3;
+    a.rho_p = h->staging + 4 * n3;
+    void* args[] = {&a};
+    LBM_CUDA(cudaLaunchKernel(h->ks->get_fields, dim3(flat_grid(h)), dim3(256), args, 0, h->stream), "get_fields");
+    if (rho) LBM_CUDA(cudaMemcpyAsync(rho, a.rho, n3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy rho");
+    if (u) LBM_CUDA(cudaMemcpyAsync(u, a.u, 3 * n3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy u");
+    if (rho_p)
+        LBM_CUDA(cudaMemcpyAsync(rho_p, a.rho_p, n3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy rho_p");
+    LBM_CUDA(cudaStreamSynchronize(h->stream), "get_fields");
+    return LBM_OK;
+}
+
+int lbm_get_populations(lbm_handle h, double* f, double* g)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!f || !g) return fail(LBM_EINVAL, "null output");
+    if (!h->initialized) return fail(LBM_ESTATE, "populations requested before initialisation");
+    const size_t n3 = h->geo.n3;
+    const size_t nq = (size_t)h->q.qf + h->q.qg;
+    if ((rc = ensure_staging(h, nq * n3 * sizeof(double)))) return rc;
+    PopArgs a;
+    a.f = f_ptr(h);
+    a.g = g_ptr(h);
+    a.geo = h->geo;
+    a.fout = h->staging;
+    a.gout = h->staging + (size_t)h->q.qf * n3;
+    a.rho0 = h->p.rho0;
+    a.odd = h->odd;
+    void* args[] = {&a};
+    LBM_CUDA(cudaLaunchKernel(h->ks->get_pops, dim3(flat_grid(h)), dim3(256), args, 0, h->stream), "get_pops");
+    LBM_CUDA(cudaMemcpyAsync(f, a.fout, (size_t)h->q.qf * n3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+             "copy f");
+    LBM_CUDA(cudaMemcpyAsync(g, a.gout, (size_t)h->q.qg * n3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+             "copy g");
+    LBM_CUDA(cudaStreamSynchronize(h->stream), "get_populations");
+    return LBM_OK;
+}
+
+int lbm_sample_populations(lbm_handle h, const int64_t* nodes, int64_t count, double* f, double* g)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (count < 0 || (count > 0 && (!nodes || !f || !g))) return fail(LBM_EINVAL, "invalid sample arguments");
+    if (!h->initialized) return fail(LBM_ESTATE, "populations requested before initialisation");
+    if (count == 0) return LBM_OK;
+    for (int64_t s = 0; s < count; ++s)
+        if (nodes[s] < 0 || nodes[s] >= (int64_t)h->geo.n3)
+            return fail(LBM_EINVAL, "node index %lld out of range", (long long)nodes[s]);
+    const size_t nq = (size_t)h->q.qf + h->q.qg;
+    const size_t bytes = (size_t)count * (nq * sizeof(double) + sizeof(int64_t));
+    if ((rc = ensure_staging(h, bytes))) return rc;
+    SampleArgs a;
+    a.f = f_ptr(h);
+    a.g = g_ptr(h);
+    a.geo = h->geo;
+    a.fout = h->staging;
+    a.gout = h->staging + (size_t)count * h->q.qf;
+    int64_t* dnodes = reinterpret_cast<int64_t*>(h->staging + (size_t)count * nq);
+    a.nodes = dnodes;
+    a.count = count;
+    a.rho0 = h->p.rho0;
+    a.odd = h->odd;
+    LBM_CUDA(cudaMemcpyAsync(dnodes, nodes, (size_t)count * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream),
+             "copy nodes");
+    void* args[] = {&a};
+    const unsigned blocks = (unsigned)((count + 255) / 256 < 4096 ? (count + 255) / 256 : 4096);
+    LBM_CUDA(cudaLaunchKernel(h->ks->sample_pops, dim3(blocks), dim3(256), args, 0, h->stream), "sample_pops");
+    LBM_CUDA(cudaMemcpyAsync(f, a.fout, (size_t)count * h->q.qf * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+             "copy f");
+    LBM_CUDA(cudaMemcpyAsync(g, a.gout, (size_t)count * h->q.qg * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+             "copy g");
+    LBM_CUDA(cudaStreamSynchronize(h->stream), "sample_populations");
+    return LBM_OK;
+}
+
+int lbm_set_populations(lbm_handle h, const double* f, const double* g)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!f || !g) return fail(LBM_EINVAL, "null input");
+    if ((rc = ensure_store(h))) return rc;
+    const size_t n3 = h->geo.n3;
+    const size_t nq = (size_t)h->q.qf + h->q.qg;
+    if ((rc = ensure_staging(h, nq * n3 * sizeof(double)))) return rc;
+    PopArgs a;
+    a.f = f_ptr(h);
+    a.g = g_ptr(h);
+    a.geo = h->geo;
+    a.fout = h->staging;
+    a.gout = h->staging + (size_t)h->q.qf * n3;
+    a.rho0 = h->p.rho0;
+    a.odd = 0;
+    LBM_CUDA(cudaMemcpyAsync(a.fout, f, (size_t)h->q.qf * n3 * sizeof(double), cudaMemcpyHostToDevice, h->stream),
+             "copy f");
+    LBM_CUDA(cudaMemcpyAsync(a.gout, g, (size_t)h->q.qg * n3 * sizeof(double), cudaMemcpyHostToDevice, h->stream),
+             "copy g");
+    void* args[] = {&a};
+    LBM_CUDA(cudaLaunchKernel(h->ks->set_pops, dim3(flat_grid(h)), dim3(256), args, 0, h->stream), "set_pops");
+    LBM_CUDA(cudaStreamSynchronize(h->stream), "set_populations");
+    h->initialized = true;
+    h->odd = 0;
+    return LBM_OK;
+}
+
+int lbm_step_count(lbm_handle h, int64_t* step)
+{
+    if (!h || !step) return fail(LBM_EINVAL, "null argument");
+    *step = h->step;
+    return LBM_OK;
+}
+
+int lbm_set_block(lbm_handle h, int bx, int by)
+{
+    if (!h) return fail(LBM_EINVAL, "null handle");
+    if (bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 256)
+        return fail(LBM_EINVAL, "block (%d, %d): bx must be a positive multiple of 32 and bx*by <= 256", bx, by);
+    h->bx = bx;
+    h->by = by;
+    drop_graph(h);
+    return LBM_OK;
+}
+
+int lbm_get_block(lbm_handle h, int* bx, int* by)
+{
+    if (!h || !bx || !by) return fail(LBM_EINVAL, "null argument");
+    *bx = h->bx;
+    *by = h->by;
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_handle h, int reps, double* best_ms_per_step)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!h->initialized) return fail(LBM_ESTATE, "autotune needs an initialised state");
+    if (reps < 1) return fail(LBM_EINVAL, "reps must be >= 1");
+    static const int cand[][2] = {{32, 1}, {32, 2}, {32, 4}, {32, 8}, {64, 1}, {64, 2}, {64, 4},
+                                  {128, 1}, {128, 2}, {256, 1}};
+    void* backup = nullptr;
+    size_t bytes = (size_t)(h->q.qf + h->q.qg) * h->geo.n3 * elem_size(h->p.storage);
+    LBM_CUDA(cudaMalloc(&backup, bytes), "autotune backup allocation");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaMemcpyAsync(backup, h->store, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    const int save_bx = h->bx, save_by = h->by, save_odd = h->odd;
+    double best = 1e300;
+    int bbx = save_bx, bby = save_by;
+    cudaError_t err = cudaSuccess;
+    for (const auto& c : cand) {
+        if (c[0] > 32 && c[0] / 2 >= h->p.nx) continue;  // wider than the row
+        if (c[1] > 1 && (c[1] / 2) >= h->p.ny) continue;
+        h->bx = c[0];
+        h->by = c[1];
+        // warm-up pair, then timed pairs
+        for (int s = 0; s < 2 && err == cudaSuccess; ++s) err = launch_step(h, (save_odd + s) & 1, h->stream);
+        cudaEventRecord(e0, h->stream);
+        for (int s = 0; s < 2 * reps && err == cudaSuccess; ++s) err = launch_step(h, (save_odd + s) & 1, h->stream);
+        cudaEventRecord(e1, h->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        if (err != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        double per = ms / (2.0 * reps);
+        if (per < best) {
+            best = per;
+            bbx = c[0];
+            bby = c[1];
+        }
+    }
+    cudaMemcpyAsync(h->store, backup, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    cudaFree(backup);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->odd = save_odd;
+    if (err != cudaSuccess) {
+        h->bx = save_bx;
+        h->by = save_by;
+        return cuda_fail(err, "autotune");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "autotune restore");
+    h->bx = bbx;
+    h->by = bby;
+    drop_graph(h);
+    if (best_ms_per_step) *best_ms_per_step = best;
+    return LBM_OK;
+}
+
+int lbm_set_graphs(lbm_handle h, int enable)
+{
+    if (!h) return fail(LBM_EINVAL, "null handle");
+    h->graphs = enable != 0;
+    if (!h->graphs) drop_graph(h);
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_handle h)
+{
+    if (!h) return LBM_OK;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graph(h);
+    if (h->own_store && h->store) cudaFree(h->store);
+    if (h->staging) cudaFree(h->staging);
+    if (h->diag_fields) cudaFree(h->diag_fields);
+    if (h->diag_partials) cudaFree(h->diag_partials);
+    if (h->diag_out) cudaFree(h->diag_out);
+    if (h->diag_host) cudaFreeHost(h->diag_host);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return LBM_OK;
+}
+
+}  // extern "C"

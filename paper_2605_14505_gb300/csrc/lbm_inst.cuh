@@ -1,0 +1,29 @@
+// Instantiation helper: defines the kernel table of one (pair, storage).
+#pragma once
+
+#include "lbm_dispatch.h"
+#include "lbm_kernels.cuh"
+
+#define LBM_STEP_PAIR(P, F, T) {(const void*)k_step<P, F, T, false>, (const void*)k_step<P, F, T, true>}
+
+#define LBM_DEFINE_KERNEL_SET(NAME, QF_, QG_, T)                                                   \
+    namespace lbm {                                                                               \
+    const KernelSet* NAME()                                                                       \
+    {                                                                                             \
+        using P = Pair<QF_, QG_>;                                                                 \
+        static const KernelSet ks = {                                                             \
+            QF_,                                                                                  \
+            QG_,                                                                                  \
+            {LBM_STEP_PAIR(P, 0, T), LBM_STEP_PAIR(P, 1, T), LBM_STEP_PAIR(P, 2, T),              \
+             LBM_STEP_PAIR(P, 3, T)},                                                             \
+            (const void*)k_init_fields<P, T>,                                                     \
+            (const void*)k_init_tgv<P, T>,                                                        \
+            (const void*)k_get_pops<P, T>,                                                        \
+            (const void*)k_set_pops<P, T>,                                                        \
+            (const void*)k_diag_moments<P, T>,                                                    \
+            (const void*)k_get_fields<P, T>,                                                      \
+            (const void*)k_sample_pops<P, T>,                                                     \
+        };                                                                                        \
+        return &ks;                                                                               \
+    }                                                                                             \
+    }

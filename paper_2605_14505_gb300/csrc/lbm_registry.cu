@@ -1,0 +1,29 @@
+// Lookup of the compiled kernel tables, and the two non-templated
+// diagnostics kernels (compiled here only).
+#define LBM_REDUCTION_KERNELS
+#include "lbm_dispatch.h"
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+const KernelSet* kernels_q27q19_f32();
+const KernelSet* kernels_q27q19_f16();
+const KernelSet* kernels_q27q19_bf16();
+const KernelSet* kernels_q19q7_f32();
+const KernelSet* kernels_q19q7_f16();
+const KernelSet* kernels_q19q7_bf16();
+
+const KernelSet* kernel_set(int pair, int storage)
+{
+    if (storage < 0 || storage > 2) return nullptr;
+    switch (pair) {
+    case 0: return storage == 0 ? kernels_q27q19_f32() : storage == 1 ? kernels_q27q19_f16() : kernels_q27q19_bf16();
+    case 1: return storage == 0 ? kernels_q19q7_f32() : storage == 1 ? kernels_q19q7_f16() : kernels_q19q7_bf16();
+    default: return nullptr;
+    }
+}
+
+const void* diag_gradients_kernel() { return (const void*)k_diag_gradients; }
+const void* diag_final_kernel() { return (const void*)k_diag_final; }
+
+}  // namespace lbm

@@ -1,0 +1,246 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Populations are compared by velocity vector (the two sides use different slot
+orders). Tolerances, FP32 storage: populations after one or two steps within
+1e-5 of their deviation scale; after 1000 steps, E_k and E_p within 1e-5
+relative (E_p relative to its maximum over the window) and velocity within
+1e-4 U0 in L-infinity. FP16/BF16 deviation storage: E_k, E_p and eps_k within
+1% of the FP64 trajectory.
+"""
+import numpy as np
+import pytest
+
+import stgv_inputs as I
+from oracle import oracle as O
+from paper_2605_14505_gb300 import lbm
+
+from _helpers import gpu_sim, lattice_params, oracle_for, rel_err, slot_map
+
+pytestmark = pytest.mark.gpu
+
+LAM = 2.0 ** -10
+
+
+def _random_pair(params, seed=5, amp=1e-3, u_amp=0.05, rp_amp=None):
+    nx, ny, nz = params.nx, params.ny, params.nz
+    n3 = nx * ny * nz
+    if rp_amp is None:
+        rp_amp = 0.02 / LAM
+    rho, u, rp = I.random_fields(nx, ny, nz, seed, u_amp, 0.01, rp_amp)
+    xf, xg = I.neq_noise(n3, seed + 1), I.neq_noise(n3, seed + 2)
+    g = gpu_sim(params)
+    g.init_fields(rho, u, rp, xf, xg, amp)
+    o = oracle_for(params)
+    o.init_fields(rho, u, rp, xf, xg, amp)
+    return g, o
+
+
+def _compare_pops(g, o, params, tol):
+    qf, qg = lbm.PAIR_Q[params.pair]
+    fg, gg = g.populations()
+    fo, go = o.populations()
+    pf, pg = slot_map(qf), slot_map(qg)
+    _, wf, _ = lbm.lbm_velocity_set(qf)
+    _, wg, _ = lbm.lbm_velocity_set(qg)
+    fo, go = fo[pf], go[pg]
+    sf = np.max(np.abs(fo - wf[:, None]))
+    sg = np.max(np.abs(go - params.rho0 * wg[:, None]))
+    ef = np.max(np.abs(fg - fo)) / sf
+    eg = np.max(np.abs(gg - go)) / sg
+    assert ef < tol and eg < tol, (ef, eg)
+    return ef, eg
+
+
+@pytest.mark.parametrize("pair", ["27x19", "19x7"])
+@pytest.mark.parametrize("forcing", ["guo", "sc", "edm", "hcz"])
+def test_population_parity_one_and_two_steps(pair, forcing):
+    """One step leaves the AA store in its swapped layout, two in the natural
+    one; both must read back as the oracle's populations. 40 x 12 x 6 spans two
+    32-wide tiles in x with a ragged tail and a ragged tile in y."""
+    N = 3e-3
+    p = lattice_params(40, 12, 6, pair, forcing, 0.53, 0.56, N * LAM, -N / LAM)
+    g, o = _random_pair(p)
+    _compare_pops(g, o, p, 1e-5)
+    for _ in range(2):
+        g.step(1)
+        o.step(1)
+        _compare_pops(g, o, p, 1e-5)
+
+
+@pytest.mark.parametrize("scalar_mode,sc_shift", [(1, 1.0), (0, 0.5)])
+def test_population_parity_reading_flags(scalar_mode, sc_shift):
+    """The Chai-Shi scalar pair and the Shan-Chen shift exactly as printed in Eq. 10."""
+    N = 3e-3
+    p = lattice_params(33, 7, 5, "27x19", "sc", 0.55, 0.7, N * LAM, -N / LAM, scalar_mode=scalar_mode,
+                       sc_shift=sc_shift)
+    g, o = _random_pair(p)
+    for _ in range(3):
+        g.step(1)
+        o.step(1)
+    _compare_pops(g, o, p, 1e-5)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 3, 1), (1, 1, 5), (33, 5, 3), (64, 2, 2)])
+def test_degenerate_and_ragged_shapes(shape):
+    """Single-node and thin periodic lattices (x - 1 wraps onto x itself) and a
+    ragged 33-wide row, 4 steps, against the oracle."""
+    N = 3e-3
+    p = lattice_params(*shape, "27x19", "guo", 0.6, 0.6, N * LAM, -N / LAM)
+    g, o = _random_pair(p)
+    g.step(4)
+    o.step(4)
+    _compare_pops(g, o, p, 2e-5)
+
+
+def test_zero_steps_and_call_order():
+    p = lattice_params(8, 8, 8, "27x19", "guo", 0.6, 0.6, 1e-5, -4.0)
+    g = gpu_sim(p)
+    with pytest.raises(lbm.LbmError) as ei:
+        g.step(1)
+    assert ei.value.code == -7  # LBM_ESTATE: step before init
+    with pytest.raises(lbm.LbmError) as ei:
+        g.diagnostics()
+    assert ei.value.code == -7
+    g.init_tgv(0, 0.0)
+    f0, _ = g.populations()
+    g.step(0)
+    f1, _ = g.populations()
+    assert np.array_equal(f0, f1)
+    with pytest.raises(lbm.LbmError):
+        g.step(-1)
+
+
+def test_invalid_parameters_rejected():
+    p = lattice_params(8, 8, 8, "27x19", "guo", 0.5, 0.6, 1e-5, -4.0)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_create_params(p)
+    assert ei.value.code == -1
+    p = lattice_params(8, 8, 4, "27x19", "guo", 0.6, 0.6, 1e-5, -4.0)
+    g = gpu_sim(p)
+    with pytest.raises(lbm.LbmError) as ei:
+        g.init_tgv(0, 0.0)  # the Taylor-Green box is cubic
+    assert ei.value.code == -1
+
+
+def _run_both(n, pair, forcing, Re, Fr, steps, storage="fp32", every=None, U0=0.04):
+    p = lbm.lbm_params_from_physics(n, n, n, pair, forcing, Re, Fr, 1.0, U0)
+    g = gpu_sim(p, storage)
+    o = oracle_for(p)
+    rho, u, rp = I.tgv_fields(n, U0)
+    g.init_fields(rho, u, rp)
+    o.init_fields(rho, u, rp)
+    every = every or steps
+    series = []
+    for _ in range(steps // every):
+        g.step(every)
+        o.step(every)
+        series.append((g.diagnostics(), o.diagnostics()))
+    return p, g, o, series
+
+
+@pytest.mark.parametrize("pair,forcing", [("27x19", "sc"), ("27x19", "guo"), ("19x7", "edm")])
+def test_fp32_1000_steps_tolerances(pair, forcing):
+    """FP32 storage after 1000 steps of the 32^3 stratified TGV (Re 100, Fr 0.5):
+    E_k, E_p relative error <= 1e-5 and velocity L-inf <= 1e-4 U0."""
+    U0 = 0.04
+    p, g, o, series = _run_both(32, pair, forcing, 100.0, 0.5, 1000, every=100, U0=U0)
+    ep_max = max(s[1]["Ep"] for s in series)
+    for dg, do in series:
+        assert abs(dg["Ek"] - do["Ek"]) / do["Ek"] <= 1e-5, (dg["Ek"], do["Ek"])
+        assert abs(dg["Ep"] - do["Ep"]) / ep_max <= 1e-5, (dg["Ep"], do["Ep"])
+    _, ug, rg = g.fields()
+    _, uo, ro = o.fields()
+    assert np.max(np.abs(ug - uo)) <= 1e-4 * U0
+    assert rel_err(rg, ro) < 1e-4
+
+
+def test_c0_diagnostics_series():
+    """The 32^3, D3Q27xD3Q19, Guo, Re 100, Fr 0.5 workload for its full 200
+    steps, diagnostics every 50 steps, all estimators against the oracle."""
+    p, g, o, series = _run_both(32, "27x19", "guo", 100.0, 0.5, 200, every=50)
+    for dg, do in series:
+        for key in ("Ek", "eps_k", "eps_k_curl"):
+            assert abs(dg[key] - do[key]) / abs(do[key]) < 2e-5, (key, dg[key], do[key])
+        for key in ("Ep", "eps_p"):
+            assert abs(dg[key] - do[key]) / abs(do[key]) < 2e-4, (key, dg[key], do[key])
+        assert abs(dg["mass_f"] - do["mass_f"]) / do["mass_f"] < 1e-9
+        assert abs(dg["mass_g"] - do["mass_g"]) / do["mass_g"] < 1e-7
+        for key in ("mom_x", "mom_y", "mom_z"):
+            assert abs(dg[key] - do[key]) < 1e-6
+
+
+@pytest.mark.parametrize("storage,tol", [("fp16", 0.01), ("bf16", 0.05)])
+def test_reduced_precision_storage_error(storage, tol):
+    """FP16/BF16 deviation storage with FP32 arithmetic: E_k, E_p, eps_k within
+    `tol` of the FP64 oracle over 1000 steps of the 32^3 SC case (north-star
+    budget 1% for FP16; BF16 keeps 8 mantissa bits and is reported at 5%)."""
+    p, g, o, series = _run_both(32, "27x19", "sc", 100.0, 0.5, 1000, storage=storage, every=100)
+    ep_max = max(s[1]["Ep"] for s in series)
+    for dg, do in series:
+        assert abs(dg["Ek"] - do["Ek"]) / do["Ek"] < tol, ("Ek", dg["Ek"], do["Ek"])
+        assert abs(dg["Ep"] - do["Ep"]) / ep_max < tol, ("Ep", dg["Ep"], do["Ep"])
+        assert abs(dg["eps_k"] - do["eps_k"]) / do["eps_k"] < tol, ("eps_k", dg["eps_k"], do["eps_k"])
+
+
+def test_device_tgv_init_matches_host_generator():
+    """lbm_init_tgv (Eq. 20 + SplitMix64 noise on the device) equals
+    lbm_init_fields fed by the seeded host generator."""
+    n, U0 = 24, 0.04
+    p = lbm.lbm_params_from_physics(n, n, n, "27x19", "sc", 100.0, 0.5, 1.0, U0)
+    a = gpu_sim(p)
+    a.init_tgv(seed=1234, noise_amp=0.05)
+    b = gpu_sim(p)
+    b.init_fields(*I.tgv_fields(n, U0, seed=1234, noise_amp=0.05))
+    fa, ga = a.populations()
+    fb, gb = b.populations()
+    assert np.max(np.abs(fa - fb)) < 1e-9
+    assert np.max(np.abs(ga - gb)) < 1e-9
+
+
+def test_graph_replay_is_bitwise_eager():
+    n = 48
+    p = lbm.lbm_params_from_physics(n, n, n, "27x19", "sc", 200.0, 0.2, 1.0, 0.04)
+    a = gpu_sim(p)
+    b = gpu_sim(p)
+    lbm.lbm_set_graphs(b.h, False)
+    for s in (a, b):
+        s.init_tgv(seed=3, noise_amp=0.01)
+        s.step(129)  # 2 graph replays of 64 steps + 1 eager step for a
+    fa, ga = a.populations()
+    fb, gb = b.populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
+def test_autotune_keeps_state_and_results():
+    n = 40
+    p = lbm.lbm_params_from_physics(n, n, n, "19x7", "guo", 200.0, 0.2, 1.0, 0.04)
+    a = gpu_sim(p)
+    b = gpu_sim(p)
+    for s in (a, b):
+        s.init_tgv(seed=9, noise_amp=0.01)
+        s.step(3)
+    f0, g0 = a.populations()
+    ms = lbm.lbm_autotune(a.h, 2)
+    assert ms > 0
+    f1, g1 = a.populations()
+    assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+    assert a.step_count == 3
+    a.step(10)
+    b.step(10)  # block shape does not change the per-node arithmetic
+    assert np.array_equal(a.populations()[0], b.populations()[0])
+
+
+def test_checkpoint_roundtrip():
+    n = 16
+    p = lbm.lbm_params_from_physics(n, n, n, "27x19", "edm", 100.0, 0.3, 1.0, 0.04)
+    a = gpu_sim(p)
+    a.init_tgv(seed=2, noise_amp=0.02)
+    a.step(7)
+    f, g = a.populations()
+    b = gpu_sim(p)
+    b.set_populations(f, g)
+    a.step(5)
+    b.step(5)
+    fa, ga = a.populations()
+    fb, gb = b.populations()
+    assert np.max(np.abs(fa - fb)) == 0.0 and np.max(np.abs(ga - gb)) == 0.0
