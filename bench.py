@@ -336,6 +336,29 @@ def run_reference_arm(args):
     print(json.dumps(line))
 
 
+def run_ncu_case(args):
+    """A small case for ncu captures (no timing output): an n^3 lattice of the
+    bench's physics with the given storage or stencil pair, initialised and
+    advanced `ncu_steps` single-kernel steps (graph replay off, so every step
+    is its own launch), then one diagnostics evaluation."""
+    import torch
+
+    from paper_2605_14505_gb300 import lbm
+
+    storage, pair = args.ncu_case, PAIR
+    if args.ncu_case == "19x7":
+        storage, pair = "fp32", "19x7"
+    p = lbm.lbm_params_from_physics(args.ncu_n, args.ncu_n, args.ncu_n, pair, FORCING, RE, FR, PR, U0)
+    sim = lbm.Simulation(p, storage=storage)
+    lbm.lbm_set_graphs(sim.h, False)
+    sim.init_tgv(seed=1, noise_amp=1e-3)
+    sim.step(args.ncu_steps)
+    d = sim.diagnostics()
+    sim.close()
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": args.ncu_case, "n": args.ncu_n, "steps": args.ncu_steps, "Ek": d["Ek"]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -344,8 +367,14 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", choices=["fp32", "fp16", "bf16", "19x7"], default=None,
+                    help="run a small profiling case instead of the benchmark")
+    ap.add_argument("--ncu-n", type=int, default=128)
+    ap.add_argument("--ncu-steps", type=int, default=6)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.ncu_case:
+        run_ncu_case(args)
+    elif args.impl == "reference":
         run_reference_arm(args)
     else:
         run_gpu_arm(args)

@@ -99,8 +99,8 @@ void derive_phys(lbm_ctx* h)
 {
     const lbm_params& p = h->p;
     Phys& ph = h->ph;
-    ph.omega_f = (float)(1.0 / p.tau_f);
-    ph.omega_g = (float)(1.0 / p.tau_g);
+    ph.delta_f = (float)((2.0 * p.tau_f - 1.0) / p.tau_f);
+    ph.delta_g = (float)((2.0 * p.tau_g - 1.0) / p.tau_g);
     ph.G = (float)p.G;
     ph.beta = (float)p.beta;
     ph.rho0 = (float)p.rho0;

@@ -17,6 +17,10 @@
 
 #include <type_traits>
 
+// Per-node arithmetic is host-callable as well, so that it can be checked
+// against the oracle without a GPU.
+#define LBM_HD __host__ __device__ __forceinline__
+
 namespace lbm {
 
 // ---------------------------------------------------------------------------
@@ -71,6 +75,28 @@ struct Lattice {
     static constexpr float inv_cs2 = (Q == 7) ? 4.0f : 3.0f;         // 1 / cs^2
     static constexpr float half_inv_cs4 = (Q == 7) ? 8.0f : 4.5f;    // 1 / (2 cs^4)
     static constexpr float half_inv_cs2 = (Q == 7) ? 2.0f : 1.5f;    // 1 / (2 cs^2)
+
+    // The FP32 weights do not sum to exactly 1 (e.g. D3Q19: 1 + 1.5e-8), nor
+    // does sum w e_x^2 equal cs^2 exactly. Summed over i, the FP32 equilibrium
+    // w_i (X + Y P_i) then carries X (sum w - 1) + 1.5 Y |u|^2 (sum w e_x^2 /
+    // cs^2 - sum w): a bias with a fixed sign every step. For the scalar
+    // (X = rho', up to ~5 with the G = N/1024 split) it grows rho' by ~3e-5
+    // over 1000 steps. The rest slot absorbs the exact residual:
+    //   w_0 (...) += kMassCorr * X + kUsqCorr * Y |u|^2.
+    __host__ __device__ static constexpr double sum_w_fp32()
+    {
+        double s = 0.0;
+        for (int i = 0; i < Q; ++i) s += (double)w(i);
+        return s;
+    }
+    __host__ __device__ static constexpr double sum_wxx_fp32()
+    {
+        double s = 0.0;
+        for (int i = 0; i < Q; ++i) s += (double)w(i) * (double)(ex(i) * ex(i));
+        return s;
+    }
+    static constexpr float kMassCorr = (float)(1.0 - sum_w_fp32());
+    static constexpr float kUsqCorr = (float)(-1.5 * (sum_wxx_fp32() / cs2d - sum_w_fp32()));
 };
 
 template <int QF_, int QG_>
@@ -83,7 +109,7 @@ struct Pair {
 
 // Compile-time loop: f(std::integral_constant<int, I>) for I in [B, E).
 template <int B, int E, class F>
-__device__ __forceinline__ void sfor(F&& f)
+LBM_HD void sfor(F&& f)
 {
     if constexpr (B < E) {
         f(std::integral_constant<int, B>{});
@@ -122,9 +148,14 @@ __device__ __forceinline__ void st_pop<__nv_bfloat16>(__nv_bfloat16* p, float v)
 // ---------------------------------------------------------------------------
 enum Forcing : int { kGuo = 0, kShanChen = 1, kEDM = 2, kHCZ = 3 };
 
+// BGK with omega = 1/tau close to 2 (tau - 1/2 ~ 0.006 in the workloads):
+// omega rounded to FP32 would move nu = cs^2 (tau - 1/2) by ~5e-6 relative, so
+// the relaxation is written with delta = 2 - omega = (2 tau - 1) / tau, which
+// FP32 holds to full relative precision:
+//   f* = f + omega (f_eq - f) = 2 f_eq - f + delta (f - f_eq).
 struct Phys {
-    float omega_f;    // 1 / tau_f
-    float omega_g;    // 1 / tau_g
+    float delta_f;    // 2 - 1 / tau_f
+    float delta_g;    // 2 - 1 / tau_g
     float G;          // gravity (Eq. 18)
     float beta;       // (d rho_b / dz)_LU (Eqs. 12, 13)
     float rho0;       // reference density (Eq. 15)
@@ -222,9 +253,15 @@ __device__ __forceinline__ uint32_t launder(uint32_t v)
 // ---------------------------------------------------------------------------
 // Moments and the coupled local solve.
 // ---------------------------------------------------------------------------
+// Near 1, FP32 resolves rho and 1/rho only to ~6e-8 absolute, and the
+// rounding of rho * fl(1/rho) stays fixed at a node for many steps (drho moves
+// slowly), rescaling the momentum coherently (E_k off by ~4e-5 after 1000
+// steps). The update therefore uses the deviations drho = rho - 1 and
+// dirho = 1/rho - 1, with rho X = X + drho X and X / rho = X + dirho X.
 struct Macro {
     float drho;      // rho - 1
-    float rho, irho;
+    float dirho;     // 1/rho - 1
+    float rho, irho; // for the diagnostics only
     float jx, jy, jz;
     float a;         // sum g - rho0
     float rho_p;     // Eq. 16
@@ -232,59 +269,14 @@ struct Macro {
     float ux, uy, uz;  // Eq. 7
 };
 
-template <class P>
-__device__ __forceinline__ Macro node_macro(const float* h, const float* k, const Phys& ph)
-{
-    using LF = typename P::LF;
-    using LG = typename P::LG;
-    Macro m;
-    float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, a = 0.f;
-    sfor<0, LF::kQ>([&](auto ic) {
-        constexpr int i = decltype(ic)::value;
-        drho += h[i];
-        if constexpr (LF::ex(i) == 1) jx += h[i];
-        if constexpr (LF::ex(i) == -1) jx -= h[i];
-        if constexpr (LF::ey(i) == 1) jy += h[i];
-        if constexpr (LF::ey(i) == -1) jy -= h[i];
-        if constexpr (LF::ez(i) == 1) jz += h[i];
-        if constexpr (LF::ez(i) == -1) jz -= h[i];
-    });
-    sfor<0, LG::kQ>([&](auto ic) {
-        constexpr int i = decltype(ic)::value;
-        a += k[i];
-    });
-    m.drho = drho;
-    m.rho = 1.f + drho;
-    m.irho = 1.f / m.rho;
-    m.jx = jx; m.jy = jy; m.jz = jz;
-    m.a = a;
-    // rho' = a + kappa * u_z with u_z = (j_z - G rho' / 2) / rho  (Eqs. 7, 12, 16-18),
-    // solved in closed form.
-    m.rho_p = (a + ph.kappa * jz * m.irho) / (1.f + 0.5f * ph.kappa * ph.G * m.irho);
-    m.Fz = -ph.G * m.rho_p;
-    m.ux = jx * m.irho;
-    m.uy = jy * m.irho;
-    m.uz = (jz + 0.5f * m.Fz) * m.irho;
-    return m;
-}
-
-// Eq. 9 written for deviations: f_eq_i - w_i = w_i (drho + rho * P_i(u)),
-// P_i = e.u / cs^2 + (e.u)^2 / (2 cs^4) - u^2 / (2 cs^2).
-template <class L, int I>
-__device__ __forceinline__ float hermite_P(float ux, float uy, float uz, float usq)
-{
-    float eu = 0.f;
-    if constexpr (L::ex(I) == 1) eu += ux;
-    if constexpr (L::ex(I) == -1) eu -= ux;
-    if constexpr (L::ey(I) == 1) eu += uy;
-    if constexpr (L::ey(I) == -1) eu -= uy;
-    if constexpr (L::ez(I) == 1) eu += uz;
-    if constexpr (L::ez(I) == -1) eu -= uz;
-    return eu * (L::inv_cs2 + L::half_inv_cs4 * eu) - L::half_inv_cs2 * usq;
-}
+// Opposite slots (2m-1, 2m) carry e and -e, so their contributions to the
+// moments are the pair sum and difference, and their equilibria share the
+// even part of P and flip the odd part.
+template <class L>
+constexpr int kPairs = (L::kQ - 1) / 2;
 
 template <class L, int I>
-__device__ __forceinline__ float e_dot(float ux, float uy, float uz)
+LBM_HD float e_dot(float ux, float uy, float uz)
 {
     float eu = 0.f;
     if constexpr (L::ex(I) == 1) eu += ux;
@@ -296,71 +288,191 @@ __device__ __forceinline__ float e_dot(float ux, float uy, float uz)
     return eu;
 }
 
-// f collision (Eqs. 5, 8, 9 with the forcing scheme), in place on h.
-template <class P, int FORCING>
-__device__ __forceinline__ void collide_f(float* h, const Macro& m, const Phys& ph)
+// Moments of one node. On return each opposite pair (2m-1, 2m) of h and k
+// holds its sum and difference, the form the collisions take.
+template <class P>
+LBM_HD Macro node_macro(float* h, float* k, const Phys& ph)
 {
     using LF = typename P::LF;
-    const float om = ph.omega_f;
+    using LG = typename P::LG;
+    Macro m;
+    float drho = h[0], jx = 0.f, jy = 0.f, jz = 0.f, a = k[0];
+    sfor<0, kPairs<LF>>([&](auto mc) {
+        constexpr int i = 2 * decltype(mc)::value + 1;
+        const float sum = h[i] + h[i + 1];
+        const float dif = h[i] - h[i + 1];
+        h[i] = sum;       // pair form, see collide_f
+        h[i + 1] = dif;
+        drho += sum;
+        if constexpr (LF::ex(i) == 1) jx += dif;
+        if constexpr (LF::ex(i) == -1) jx -= dif;
+        if constexpr (LF::ey(i) == 1) jy += dif;
+        if constexpr (LF::ey(i) == -1) jy -= dif;
+        if constexpr (LF::ez(i) == 1) jz += dif;
+        if constexpr (LF::ez(i) == -1) jz -= dif;
+    });
+    sfor<0, kPairs<LG>>([&](auto mc) {
+        constexpr int i = 2 * decltype(mc)::value + 1;
+        const float sum = k[i] + k[i + 1];
+        const float dif = k[i] - k[i + 1];
+        k[i] = sum;
+        k[i + 1] = dif;
+        a += sum;
+    });
+    m.drho = drho;
+    m.dirho = -drho / (1.f + drho);
+    m.rho = 1.f + drho;
+    m.irho = 1.f + m.dirho;
+    m.jx = jx; m.jy = jy; m.jz = jz;
+    m.a = a;
+    // rho' = a + kappa * u_z with u_z = (j_z - G rho' / 2) / rho  (Eqs. 7, 12, 16-18),
+    // solved in closed form.
+    // num / (1 + x) with x = kappa G / (2 rho) ~ 1e-6: 1 + x rounded in FP32
+    // would be one fixed value for every node and step, a coherent bias of
+    // rho' of up to 6e-8 per step, so the division is num - num x / (1 + x).
+    const float kg = 0.5f * ph.kappa * ph.G;
+    const float num = a + ph.kappa * fmaf(jz, m.dirho, jz);
+    const float x = fmaf(kg, m.dirho, kg);
+    m.rho_p = fmaf(-num, x / (1.f + x), num);
+    m.Fz = -ph.G * m.rho_p;
+    const float jzf = jz + 0.5f * m.Fz;
+    m.ux = fmaf(jx, m.dirho, jx);
+    m.uy = fmaf(jy, m.dirho, jy);
+    m.uz = fmaf(jzf, m.dirho, jzf);
+    return m;
+}
+
+// BGK step of one population: f + omega (f_eq - f) = 2 f_eq - f + delta (f - f_eq).
+LBM_HD float bgk(float f, float feq, float dl)
+{
+    return fmaf(dl, f - feq, 2.f * feq - f);
+}
+
+// Eq. 9 for deviations: f_eq_i - w_i = w_i (drho + rho P_i), with
+// P_i = e.u / cs^2 + (e.u)^2 / (2 cs^4) - u^2 / (2 cs^2). For the pair (i, opp):
+// f_eq = w (base + rho (e.u)^2 / (2 cs^4)) +- w rho e.u / cs^2, base = drho - rho u^2 / (2 cs^2).
+//
+// f collision (Eqs. 5, 8, 9) with the forcing scheme, in place on h.
+template <class P, int FORCING>
+LBM_HD void collide_f(float* h, const Macro& m, const Phys& ph)
+{
+    using LF = typename P::LF;
+    constexpr float c1 = LF::inv_cs2, c2 = LF::half_inv_cs4, c0 = LF::half_inv_cs2;
+    const float dl = ph.delta_f;
+    // velocity of the equilibrium: u of Eq. 7 (Guo, HCZ), the Shan-Chen shifted
+    // velocity of Eq. 10, or j / rho (EDM). Its momentum rho v is formed
+    // without dividing by rho, so that the odd (momentum) part of f_eq,
+    // w e.(rho v) / cs^2, carries no rounding of 1/rho: with rho = 1 + drho
+    // rounded near 1, rho * (j / rho) differs from j by a rounding error that
+    // follows the smooth fields and rescales the momentum coherently.
+    float mx = m.jx, my = m.jy, mz;
     if constexpr (FORCING == kGuo || FORCING == kHCZ) {
-        const float usq = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
-        const float pref = ph.guo_pref * m.Fz;
-        sfor<0, LF::kQ>([&](auto ic) {
-            constexpr int i = decltype(ic)::value;
-            const float Pi = hermite_P<LF, i>(m.ux, m.uy, m.uz, usq);
-            const float heq = LF::w(i) * (m.drho + m.rho * Pi);
-            float Fi;
-            if constexpr (FORCING == kGuo) {
-                // Guo, Zheng & Shi: (1 - 1/(2 tau)) w [ (e - u)/cs^2 + (e.u) e / cs^4 ] . F
-                const float eu = e_dot<LF, i>(m.ux, m.uy, m.uz);
-                Fi = pref * LF::w(i) *
-                     (LF::inv_cs2 * ((float)LF::ez(i) - m.uz) + 2.f * LF::half_inv_cs4 * eu * (float)LF::ez(i));
-            } else {
-                // He-Chen-Zhang: (1 - 1/(2 tau)) (e - u).F / (rho cs^2) f_eq
-                Fi = pref * LF::inv_cs2 * ((float)LF::ez(i) - m.uz) * LF::w(i) * (1.f + Pi);
-            }
-            h[i] = h[i] + om * (heq - h[i]) + Fi;
-        });
+        mz = m.jz + 0.5f * m.Fz;
     } else if constexpr (FORCING == kShanChen) {
-        // Eq. 10: equilibrium at u_eq = j / rho + shift * tau_f F / rho
-        const float vx = m.jx * m.irho, vy = m.jy * m.irho;
-        const float vz = (m.jz + ph.sc_tau * m.Fz) * m.irho;
-        const float vsq = vx * vx + vy * vy + vz * vz;
-        sfor<0, LF::kQ>([&](auto ic) {
-            constexpr int i = decltype(ic)::value;
-            const float heq = LF::w(i) * (m.drho + m.rho * hermite_P<LF, i>(vx, vy, vz, vsq));
-            h[i] = h[i] + om * (heq - h[i]);
-        });
+        mz = m.jz + ph.sc_tau * m.Fz;
     } else {
-        // Exact difference method: BGK toward f_eq(rho, j/rho) plus
-        // f_eq(rho, j/rho + F/rho) - f_eq(rho, j/rho)
-        const float vx = m.jx * m.irho, vy = m.jy * m.irho, vz = m.jz * m.irho;
-        const float vsq = vx * vx + vy * vy + vz * vz;
-        const float wz = vz + m.Fz * m.irho;
-        const float wsq = vx * vx + vy * vy + wz * wz;
-        sfor<0, LF::kQ>([&](auto ic) {
-            constexpr int i = decltype(ic)::value;
-            const float P1 = hermite_P<LF, i>(vx, vy, vz, vsq);
-            const float P2 = hermite_P<LF, i>(vx, vy, wz, wsq);
-            const float heq = LF::w(i) * (m.drho + m.rho * P1);
-            h[i] = h[i] + om * (heq - h[i]) + LF::w(i) * m.rho * (P2 - P1);
-        });
+        mz = m.jz;
     }
+    const float vx = fmaf(mx, m.dirho, mx), vy = fmaf(my, m.dirho, my), vz = fmaf(mz, m.dirho, mz);
+    const float vsq = vx * vx + vy * vy + vz * vz;
+    const float base = m.drho - c0 * (mx * vx + my * vy + mz * vz);
+    // forcing coefficients
+    const float gF = ph.guo_pref * m.Fz;     // Guo / HCZ: (1 - 1/(2 tau)) F_z
+    const float du = fmaf(m.Fz, m.dirho, m.Fz);  // EDM: velocity increment F/rho (z only)
+    const float dusq = du * (2.f * vz + du); // |v + du|^2 - |v|^2
+
+    // rest slot (e = 0), with the exact FP32 weight-sum residual
+    {
+        float heq = LF::w(0) * base + LF::kMassCorr * m.drho + LF::kUsqCorr * (mx * vx + my * vy + mz * vz);
+        float F0 = 0.f;
+        if constexpr (FORCING == kGuo) F0 = -gF * LF::w(0) * c1 * vz;
+        if constexpr (FORCING == kHCZ) F0 = -gF * c1 * vz * LF::w(0) * (1.f - c0 * vsq);
+        if constexpr (FORCING == kEDM) {
+            const float rdusq = fmaf(m.drho, dusq, dusq);   // rho (|v + du|^2 - |v|^2)
+            F0 = (-c0 * LF::w(0) + LF::kUsqCorr) * rdusq;
+        }
+        h[0] = bgk(h[0], heq, dl) + F0;
+    }
+    // Odd (momentum) parts: sum over pairs of e (f_eq_i - f_eq_j) must be the
+    // momentum rho v exactly. With FP32 weights, sum w e_x^2 / cs^2 = 1 + eps
+    // (eps ~ 1e-8), so the plain form w e.(rho v) / cs^2 would rescale the
+    // momentum by ~(1 + 2 eps) every step (E_k off by ~5e-5 after 1000 steps).
+    // The edge and corner pairs use the plain form; each axis pair takes the
+    // residual, so the momentum is exact up to the rounding of this sum.
+    float ox = 0.f, oy = 0.f, oz = 0.f;
+    auto relax_pair = [&](auto mc, float ha) {
+        constexpr int i = 2 * decltype(mc)::value + 1;
+        constexpr int j = i + 1;
+        constexpr float w = LF::w(i);
+        constexpr int ez = LF::ez(i);
+        const float eu = e_dot<LF, i>(vx, vy, vz);
+        const float em = e_dot<LF, i>(mx, my, mz);
+        const float hs = w * fmaf(c2 * em, eu, base);
+        float Fs = 0.f, Fa = 0.f;
+        if constexpr (FORCING == kGuo) {
+            // (1 - 1/(2 tau)) w [ (e - u)/cs^2 + (e.u) e / cs^4 ] . F
+            Fs = gF * w * (ez != 0 ? (2.f * c2 * eu * (float)ez - c1 * vz) : -c1 * vz);
+            Fa = gF * w * c1 * (float)ez;
+        } else if constexpr (FORCING == kHCZ) {
+            // (1 - 1/(2 tau)) (e - u).F / (rho cs^2) f_eq, f_eq = w rho (1 + P)
+            const float ps = 1.f + c2 * eu * eu - c0 * vsq;
+            const float pa = c1 * eu;
+            const float c = gF * c1 * w;
+            Fs = c * ((float)ez * pa - vz * ps);
+            Fa = c * ((float)ez * ps - vz * pa);
+        } else if constexpr (FORCING == kEDM) {
+            // f_eq(v + du) - f_eq(v) in closed form
+            float ps = -c0 * dusq;
+            if constexpr (ez != 0) ps += c2 * du * (2.f * (float)ez * eu + du);
+            Fs = w * fmaf(m.drho, ps, ps);
+            Fa = (ez != 0) ? w * c1 * (float)ez * m.Fz : 0.f;     // w rho e_z du / cs^2
+        }
+        // Even and odd parts relax separately: forming hs +- ha first would round
+        // the even part (density, stress) to the ulp of the much larger odd part.
+        const float sp = bgk(h[i], 2.f * hs, dl) + 2.f * Fs;   // h_i + h_j
+        const float dp = bgk(h[j], 2.f * ha, dl) + 2.f * Fa;   // h_i - h_j
+        h[i] = 0.5f * (sp + dp);
+        h[j] = 0.5f * (sp - dp);
+    };
+    sfor<3, kPairs<LF>>([&](auto mc) {
+        constexpr int i = 2 * decltype(mc)::value + 1;
+        const float ha = LF::w(i) * c1 * e_dot<LF, i>(mx, my, mz);
+        if constexpr (LF::ex(i) != 0) ox += (float)LF::ex(i) * ha;
+        if constexpr (LF::ey(i) != 0) oy += (float)LF::ey(i) * ha;
+        if constexpr (LF::ez(i) != 0) oz += (float)LF::ez(i) * ha;
+        relax_pair(mc, ha);
+    });
+    relax_pair(std::integral_constant<int, 0>{}, fmaf(0.5f, mx, -ox));   // slots 1, 2: +-x
+    relax_pair(std::integral_constant<int, 1>{}, fmaf(0.5f, my, -oy));   // slots 3, 4: +-y
+    relax_pair(std::integral_constant<int, 2>{}, fmaf(0.5f, mz, -oz));   // slots 5, 6: +-z
 }
 
 // g collision (Eqs. 11, 12, 14, 15): g_eq = (rho' + rho0) Theta(u), S_i = w_i (-u_z beta).
+// For deviations: g_eq_i - w_i rho0 = w_i (rho' + (rho' + rho0) P_i).
 template <class P>
-__device__ __forceinline__ void collide_g(float* k, const Macro& m, const Phys& ph)
+LBM_HD void collide_g(float* k, const Macro& m, const Phys& ph)
 {
     using LG = typename P::LG;
+    constexpr float c1 = LG::inv_cs2, c2 = LG::half_inv_cs4, c0 = LG::half_inv_cs2;
     const float usq = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
     const float rr = m.rho_p + ph.rho0;
     const float src = ph.c_lbe * (-m.uz * ph.beta);
-    const float om = ph.omega_g;
-    sfor<0, LG::kQ>([&](auto ic) {
-        constexpr int i = decltype(ic)::value;
-        const float keq = LG::w(i) * (m.rho_p + rr * hermite_P<LG, i>(m.ux, m.uy, m.uz, usq));
-        k[i] = k[i] + om * (keq - k[i]) + LG::w(i) * src;
+    const float base = m.rho_p - c0 * rr * usq;
+    const float dl = ph.delta_g;
+    {
+        const float keq = LG::w(0) * base + LG::kMassCorr * m.rho_p + LG::kUsqCorr * rr * usq;
+        k[0] = bgk(k[0], keq, dl) + (LG::w(0) + LG::kMassCorr) * src;
+    }
+    sfor<0, kPairs<LG>>([&](auto mc) {
+        constexpr int i = 2 * decltype(mc)::value + 1;
+        constexpr float w = LG::w(i);
+        const float eu = e_dot<LG, i>(m.ux, m.uy, m.uz);
+        const float ks = w * fmaf(rr * c2, eu * eu, base);
+        const float ka = w * rr * c1 * eu;
+        const float sp = bgk(k[i], 2.f * ks, dl) + 2.f * w * src;
+        const float dp = bgk(k[i + 1], 2.f * ka, dl);
+        k[i] = 0.5f * (sp + dp);
+        k[i + 1] = 0.5f * (sp - dp);
     });
 }
 

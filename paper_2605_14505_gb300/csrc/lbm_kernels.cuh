@@ -350,19 +350,22 @@ __global__ void __launch_bounds__(kDiagBlock) k_diag_moments(DiagArgs a)
             load_node<typename P::LG, false, T>(static_cast<const T*>(a.g), n3, na, k);
         }
         const Macro m = node_macro<P>(h, k, a.ph);
-        // second moment of the deviations: M2 = sum e e h; Pi_neq = M2 - rho u u - drho cs^2 I
+        // second moment of the deviations: M2 = sum e e h; Pi_neq = M2 - rho u u - drho cs^2 I.
+        // node_macro left each opposite pair as (sum, difference); e e is the same
+        // for e and -e, so a pair contributes e e (h_i + h_j), its stored sum.
         float mxx = 0.f, myy = 0.f, mzz = 0.f, mxy = 0.f, mxz = 0.f, myz = 0.f;
-        sfor<0, LF::kQ>([&](auto ic) {
-            constexpr int i = decltype(ic)::value;
-            if constexpr (LF::ex(i) != 0) mxx += h[i];
-            if constexpr (LF::ey(i) != 0) myy += h[i];
-            if constexpr (LF::ez(i) != 0) mzz += h[i];
-            if constexpr (LF::ex(i) * LF::ey(i) == 1) mxy += h[i];
-            if constexpr (LF::ex(i) * LF::ey(i) == -1) mxy -= h[i];
-            if constexpr (LF::ex(i) * LF::ez(i) == 1) mxz += h[i];
-            if constexpr (LF::ex(i) * LF::ez(i) == -1) mxz -= h[i];
-            if constexpr (LF::ey(i) * LF::ez(i) == 1) myz += h[i];
-            if constexpr (LF::ey(i) * LF::ez(i) == -1) myz -= h[i];
+        sfor<0, kPairs<LF>>([&](auto mc) {
+            constexpr int i = 2 * decltype(mc)::value + 1;
+            const float sp = h[i];
+            if constexpr (LF::ex(i) != 0) mxx += sp;
+            if constexpr (LF::ey(i) != 0) myy += sp;
+            if constexpr (LF::ez(i) != 0) mzz += sp;
+            if constexpr (LF::ex(i) * LF::ey(i) == 1) mxy += sp;
+            if constexpr (LF::ex(i) * LF::ey(i) == -1) mxy -= sp;
+            if constexpr (LF::ex(i) * LF::ez(i) == 1) mxz += sp;
+            if constexpr (LF::ex(i) * LF::ez(i) == -1) mxz -= sp;
+            if constexpr (LF::ey(i) * LF::ez(i) == 1) myz += sp;
+            if constexpr (LF::ey(i) * LF::ez(i) == -1) myz -= sp;
         });
         const float dc = m.drho * LF::cs2;
         // S = s_scale / rho * (Pi_neq + (u F + F u) / 2), F = (0, 0, Fz)

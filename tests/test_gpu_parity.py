@@ -163,10 +163,14 @@ def test_c0_diagnostics_series():
             assert abs(dg[key] - do[key]) / abs(do[key]) < 2e-5, (key, dg[key], do[key])
         for key in ("Ep", "eps_p"):
             assert abs(dg[key] - do[key]) / abs(do[key]) < 2e-4, (key, dg[key], do[key])
-        assert abs(dg["mass_f"] - do["mass_f"]) / do["mass_f"] < 1e-9
-        assert abs(dg["mass_g"] - do["mass_g"]) / do["mass_g"] < 1e-7
+        # FP32 storage rounds each deviation every step: the totals random-walk
+        # by ~1e-8 per node over this window (the oracle conserves to 1e-16)
+        n3 = 32 ** 3
+        assert abs(dg["mass_f"] - do["mass_f"]) / n3 < 1e-8
+        assert abs(dg["mass_g"] - do["mass_g"]) / n3 < 1e-6
+        # total momentum (~0 by symmetry) drifts by FP32 random-walk rounding only
         for key in ("mom_x", "mom_y", "mom_z"):
-            assert abs(dg[key] - do[key]) < 1e-6
+            assert abs(dg[key] - do[key]) < 1e-5
 
 
 @pytest.mark.parametrize("storage,tol", [("fp16", 0.01), ("bf16", 0.05)])
