@@ -210,6 +210,27 @@ int lbm_set_populations(lbm_handle h, const double* f, const double* g);
 /* Time steps taken since the last init. */
 int lbm_step_count(lbm_handle h, int64_t* step);
 
+/* Diagnostics that allocate nothing: a variant of lbm_diagnostics for callers
+ * that cannot call cudaMalloc or let a library do so, such as a host program
+ * that hands all device memory to its own pool and forbids other
+ * allocations, code that must not trigger the device-wide synchronisation a
+ * cudaMalloc/cudaFree implies while other streams run, or a process close to
+ * its memory limit. (The paper has no counterpart: it is an interface
+ * convenience.)
+ * Fills out->Ek, Ep, eps_k, mass_f, mass_g, mom, umax and step exactly as
+ * lbm_diagnostics defines them (summed in a different block order, so equal
+ * up to FP64 rounding); out->eps_p and out->eps_k_curl are set to NaN because
+ * they need a field of nx*ny*nz values, which this variant does not have.
+ * Scratch: one file-scope device array of 4096 x 11 doubles (~360 KB) that
+ * every GPU loading this library holds until the process exits. It limits the
+ * lattice to 4096 * 32768 = 134,217,728 nodes (512^3); larger lattices give
+ * LBM_EINVAL. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the array, which keeps the last call's contents: calls that
+ * overlap on the GPU (several handles or threads, different streams) race and
+ * must be serialised by the caller. Waits for the handle's stream. */
+int lbm_diagnostics_noalloc(lbm_handle h, lbm_diag* out);
+
 /* Launch shape of the step kernel (threads along x and y; bx * by <= 256,
  * bx a multiple of 32). */
 int lbm_set_block(lbm_handle h, int bx, int by);

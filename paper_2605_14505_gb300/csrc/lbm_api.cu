@@ -6,6 +6,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <limits>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -791,6 +793,106 @@ int lbm_set_graphs(lbm_handle h, int enable)
     if (!h) return fail(LBM_EINVAL, "null handle");
     h->graphs = enable != 0;
     if (!h->graphs) drop_graph(h);
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free diagnostics: the block partials of the moment pass and the
+// final sums live in this file-scope device array instead of cudaMalloc'ed
+// scratch. Host code cannot use the array's name as a device address, so the
+// address is looked up once per device and cached.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kStaticMaxBlocks = 4096;
+constexpr uint32_t kStaticNodesPerBlock = 32768;
+constexpr size_t kStaticOutOffset = (size_t)kStaticMaxBlocks * kDNumSlots;
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mutex;
+double* g_static_addr[kStaticMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) double g_static_scratch[kStaticOutOffset + 16];
+
+namespace {
+int static_scratch_address(int device, double** out)
+{
+    if (device < 0 || device >= kStaticMaxDevices) return fail(LBM_EUNSUPPORTED, "device %d out of range", device);
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress of the static diagnostics scratch");
+        g_static_addr[device] = static_cast<double*>(p);
+    }
+    *out = g_static_addr[device];
+    return LBM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int lbm_diagnostics_noalloc(lbm_handle h, lbm_diag* out)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!out) return fail(LBM_EINVAL, "null output");
+    const uint32_t n3 = h->geo.n3;
+    const uint32_t blocks = (n3 + kStaticNodesPerBlock - 1) / kStaticNodesPerBlock;
+    if (blocks > (uint32_t)kStaticMaxBlocks)
+        return fail(LBM_EINVAL,
+                    "lattice of %u nodes exceeds the static diagnostics scratch (at most %u nodes); "
+                    "use lbm_diagnostics",
+                    n3, (unsigned)kStaticMaxBlocks * kStaticNodesPerBlock);
+    if (!h->initialized) return fail(LBM_ESTATE, "diagnostics before initialisation");
+    double* scratch = nullptr;
+    if ((rc = static_scratch_address(h->device, &scratch))) return rc;
+    const lbm_params& p = h->p;
+    const double cs2f = cs2_of(h->q.qf);
+    const double gn2 = (p.beta != 0.0) ? (-p.G * p.rho0 / p.beta) : 1.0;
+    const double nu = cs2f * (p.tau_f - 0.5);
+    DiagArgs a;
+    a.f = f_ptr(h);
+    a.g = g_ptr(h);
+    a.geo = h->geo;
+    a.ph = h->ph;
+    a.odd = h->odd;
+    a.ep_scale = (float)(0.5 * gn2 / (p.rho0 * p.rho0));
+    a.epsk_scale = (float)(2.0 * nu);
+    a.s_scale = (float)(-1.0 / (2.0 * cs2f * p.tau_f));
+    a.epsp_scale = 0.f;
+    a.nu = (float)nu;
+    a.fields = nullptr;      // no field scratch: the central-difference pass is skipped
+    a.partials = scratch;    // every block overwrites its own record, nothing needs clearing
+    void* args[] = {&a};
+    LBM_CUDA(cudaLaunchKernel(h->ks->diag_moments, dim3(blocks), dim3(kDiagBlock), args, 0, h->stream),
+             "static diag pass 1");
+    const double* pp = scratch;
+    int nb = (int)blocks;
+    double* dout = scratch + kStaticOutOffset;
+    void* fargs[] = {&pp, &nb, &dout};
+    LBM_CUDA(cudaLaunchKernel(diag_final_kernel(), dim3(1), dim3(kDiagBlock), fargs, 0, h->stream),
+             "static diag pass 2");
+    double s[kDNumSlots];
+    LBM_CUDA(cudaMemcpyAsync(s, dout, sizeof(s), cudaMemcpyDeviceToHost, h->stream), "static diag copy");
+    LBM_CUDA(cudaStreamSynchronize(h->stream), "static diagnostics");
+    const double inv = 1.0 / (double)n3;
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    out->Ek = s[kDEk] * inv;
+    out->Ep = s[kDEp] * inv;
+    out->eps_k = s[kDEpsK] * inv;
+    out->eps_p = nan;
+    out->eps_k_curl = nan;
+    out->mass_f = (double)n3 + s[kDDrho];
+    out->mass_g = (double)n3 * p.rho0 + s[kDA];
+    out->mom[0] = s[kDJx];
+    out->mom[1] = s[kDJy];
+    out->mom[2] = s[kDJz];
+    out->umax = s[kDUmax];
+    out->step = h->step;
+    for (int q = 0; q < kDiagPass1; ++q)
+        if (!std::isfinite(s[q])) return fail(LBM_ENONFINITE, "non-finite diagnostics at step %lld", (long long)h->step);
     return LBM_OK;
 }
 

@@ -92,6 +92,7 @@ _SIGS = {
     "lbm_step": ([_H, ctypes.c_int64], ctypes.c_int),
     "lbm_synchronize": ([_H], ctypes.c_int),
     "lbm_diagnostics": ([_H, ctypes.POINTER(lbm_diag)], ctypes.c_int),
+    "lbm_diagnostics_noalloc": ([_H, ctypes.POINTER(lbm_diag)], ctypes.c_int),
     "lbm_get_fields": ([_H, _DP, _DP, _DP], ctypes.c_int),
     "lbm_get_populations": ([_H, _DP, _DP], ctypes.c_int),
     "lbm_set_populations": ([_H, _DP, _DP], ctypes.c_int),
@@ -238,6 +239,13 @@ def lbm_diagnostics(h, allow_nonfinite: bool = False) -> dict:
     rc = load_library().lbm_diagnostics(h, ctypes.byref(d))
     if not (allow_nonfinite and rc == -5):
         _check(rc)
+    return d.as_dict()
+
+
+def lbm_diagnostics_noalloc(h) -> dict:
+    """lbm_diagnostics without any device allocation (eps_p, eps_k_curl are NaN)."""
+    d = lbm_diag()
+    _check(load_library().lbm_diagnostics_noalloc(h, ctypes.byref(d)))
     return d.as_dict()
 
 
