@@ -247,6 +247,75 @@ int lbm_set_graphs(lbm_handle h, int enable);
 /* Free the handle and every library-owned device buffer. NULL is allowed. */
 int lbm_destroy(lbm_handle h);
 
+/* ---- Batched instances -------------------------------------------------
+ * A parameter sweep of the paper's kind (Sections 3.2-3.6: stencil pairs,
+ * forcing schemes, Froude numbers, resolutions) as many independent periodic
+ * lattices advanced by one launch per step, or by one persistent cooperative
+ * launch per `steps_per_launch` steps with a bounded grid barrier between
+ * steps. Instances may differ in size, pair (D3Q27xD3Q19, D3Q19xD3Q7),
+ * forcing and parameters; storage is FP32. Each instance's arithmetic is the
+ * single-lattice update's. */
+typedef struct lbm_batch_ctx* lbm_batch;
+
+enum lbm_batch_mode { LBM_BATCH_PERSISTENT = 0, LBM_BATCH_PER_STEP = 1 };
+
+/* Create `count` (1..65535) instances from lattice parameters (copied) and
+ * allocate their stores on the current device. LBM_EUNSUPPORTED for a
+ * storage other than FP32 or a pair other than the two above. */
+int lbm_batch_create(lbm_batch* out, const lbm_params* params, int count);
+
+/* Number of instances. */
+int lbm_batch_count(lbm_batch b, int* count);
+
+/* Handle of instance i (owned by the batch: never lbm_destroy it). Use it
+ * for lbm_get_fields, lbm_get_populations, lbm_sample_populations or
+ * lbm_diagnostics of that instance; lbm_step on it advances it alone. */
+int lbm_batch_instance(lbm_batch b, int i, lbm_handle* h);
+
+/* Stream for all batch work (not owned; NULL disables graph replay). */
+int lbm_batch_set_stream(lbm_batch b, void* stream);
+
+/* LBM_BATCH_PERSISTENT (default; steps_per_launch steps per cooperative
+ * launch, default 100) or LBM_BATCH_PER_STEP (one launch per step, replayed
+ * from a CUDA graph of 64 steps). */
+int lbm_batch_set_mode(lbm_batch b, int mode, int steps_per_launch);
+
+/* Tile shape: bx in {16, 32, 64, 128} nodes along x, by along y, bx*by a
+ * multiple of 32 and <= 256 (default 32 x 8). */
+int lbm_batch_set_block(lbm_batch b, int bx, int by);
+
+/* Current tile shape, mode and grid size (blocks of the persistent launch,
+ * or tiles for per-step launches). Pointers may be NULL. */
+int lbm_batch_get_config(lbm_batch b, int* bx, int* by, int* mode, int* grid);
+
+/* lbm_init_tgv on every instance (same seed and noise amplitude). */
+int lbm_batch_init_tgv(lbm_batch b, uint64_t seed, double noise_amp);
+
+/* Advance every instance by nsteps >= 0 steps, asynchronously. */
+int lbm_batch_step(lbm_batch b, int64_t nsteps);
+
+/* Wait for the batch stream. LBM_ETIMEOUT if a grid-barrier wait of a
+ * persistent launch ran out (the kernel then ended early and the instances'
+ * state is undefined); the flag is cleared. */
+int lbm_batch_synchronize(lbm_batch b);
+
+/* lbm_diagnostics of every instance into out[count] (waits; LBM_ETIMEOUT as
+ * lbm_batch_synchronize; LBM_ENONFINITE if any instance has NaN/Inf). */
+int lbm_batch_diagnostics(lbm_batch b, lbm_diag* out);
+
+/* Time every tile shape and both modes (reps step pairs each, CUDA events)
+ * and keep the fastest; the instances' state is saved and restored.
+ * best_ms_per_step may be NULL. */
+int lbm_batch_autotune(lbm_batch b, int reps, double* best_ms_per_step);
+
+/* Fault-injection hook for tests of the timeout path: make each grid
+ * barrier wait for `extra_blocks` arrivals that never come and give up after
+ * `spin_limit` polls (default 0 and 4194304). */
+int lbm_batch_set_barrier_test(lbm_batch b, unsigned extra_blocks, unsigned spin_limit);
+
+/* Free the batch, its instances and their stores. NULL is allowed. */
+int lbm_batch_destroy(lbm_batch b);
+
 #ifdef __cplusplus
 }
 #endif

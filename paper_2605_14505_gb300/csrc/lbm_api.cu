@@ -10,6 +10,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "lbm_dispatch.h"
@@ -910,6 +911,426 @@ int lbm_destroy(lbm_handle h)
     if (h->diag_host) cudaFreeHost(h->diag_host);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched instances: many independent lattices advanced by one launch.
+// ---------------------------------------------------------------------------
+struct lbm_batch_ctx {
+    std::vector<lbm_ctx*> inst;
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    BatchInstance* d_inst = nullptr;
+    uint16_t* d_tile = nullptr;
+    unsigned* d_sync = nullptr;
+    uint32_t ntiles = 0;
+    int bx = 32, by = 8;
+    int mode = LBM_BATCH_PERSISTENT;
+    int chunk = 100;
+    int persistent_grid = 0;
+    unsigned spin_limit = 1u << 22;   // ~0.3-1 s of polling at 64 ns naps
+    unsigned extra_blocks = 0;        // test hook: barrier arrivals that never come
+    bool initialized = false;
+    int64_t step = 0;
+    int odd = 0;
+    cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+constexpr int kBatchGraphSteps = 64;
+
+void batch_drop_graph(lbm_batch_ctx* b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+int batch_build_tiles(lbm_batch_ctx* b)
+{
+    std::vector<BatchInstance> hi(b->inst.size());
+    std::vector<uint16_t> tiles;
+    uint32_t t0 = 0;
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        lbm_ctx* h = b->inst[i];
+        BatchInstance& I = hi[i];
+        I.f = f_ptr(h);
+        I.g = g_ptr(h);
+        I.geo = h->geo;
+        I.ph = h->ph;
+        I.variant = 4 * h->p.pair + h->p.forcing;
+        I.tx = (uint32_t)((h->p.nx + b->bx - 1) / b->bx);
+        I.ty = (uint32_t)((h->p.ny + b->by - 1) / b->by);
+        I.tile0 = t0;
+        const uint64_t n = (uint64_t)I.tx * I.ty * (uint64_t)h->p.nz;
+        if ((uint64_t)t0 + n > 0xffffffffull) return fail(LBM_EINVAL, "batch tile count exceeds 2^32");
+        tiles.insert(tiles.end(), (size_t)n, (uint16_t)i);
+        t0 += (uint32_t)n;
+    }
+    b->ntiles = t0;
+    if (b->d_inst) cudaFree(b->d_inst);
+    if (b->d_tile) cudaFree(b->d_tile);
+    b->d_inst = nullptr;
+    b->d_tile = nullptr;
+    if (cudaMalloc(&b->d_inst, hi.size() * sizeof(BatchInstance)) != cudaSuccess ||
+        cudaMalloc(&b->d_tile, tiles.size() * sizeof(uint16_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ENOMEM, "batch descriptor allocation failed");
+    }
+    LBM_CUDA(cudaMemcpy(b->d_inst, hi.data(), hi.size() * sizeof(BatchInstance), cudaMemcpyHostToDevice),
+             "copy batch descriptors");
+    LBM_CUDA(cudaMemcpy(b->d_tile, tiles.data(), tiles.size() * sizeof(uint16_t), cudaMemcpyHostToDevice),
+             "copy batch tiles");
+    int per_sm = 0;
+    LBM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persistent_kernel(), b->bx * b->by, 0),
+             "batch occupancy");
+    if (per_sm < 1) return fail(LBM_EUNSUPPORTED, "persistent batch kernel does not fit on an SM");
+    uint64_t grid = (uint64_t)per_sm * (uint64_t)b->num_sms;
+    b->persistent_grid = (int)(grid < b->ntiles ? grid : b->ntiles);
+    batch_drop_graph(b);
+    return LBM_OK;
+}
+
+BatchArgs batch_args(const lbm_batch_ctx* b, int steps, int odd0, unsigned grid)
+{
+    BatchArgs a;
+    a.inst = b->d_inst;
+    a.tile_inst = b->d_tile;
+    a.ntiles = b->ntiles;
+    a.steps = steps;
+    a.odd0 = odd0;
+    a.sync = b->d_sync;
+    a.nblocks = grid + b->extra_blocks;
+    a.spin_limit = b->spin_limit;
+    return a;
+}
+
+cudaError_t batch_launch_step(lbm_batch_ctx* b, int odd, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)(b->ntiles < (uint32_t)(b->num_sms * 64) ? b->ntiles : b->num_sms * 64);
+    BatchArgs a = batch_args(b, 1, odd, grid);
+    void* args[] = {&a};
+    return cudaLaunchKernel(batch_step_kernel(odd), dim3(grid), dim3(b->bx, b->by), args, 0, s);
+}
+
+cudaError_t batch_launch_persistent(lbm_batch_ctx* b, int steps, int odd, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)b->persistent_grid;
+    BatchArgs a = batch_args(b, steps, odd, grid);
+    void* args[] = {&a};
+    return cudaLaunchCooperativeKernel(batch_persistent_kernel(), dim3(grid), dim3(b->bx, b->by), args, 0, s);
+}
+
+void batch_sync_instances(lbm_batch_ctx* b)
+{
+    for (lbm_ctx* h : b->inst) {
+        h->step = b->step;
+        h->odd = b->odd;
+        h->initialized = b->initialized;
+    }
+}
+
+int batch_check(lbm_batch_ctx* b)
+{
+    if (!b) return fail(LBM_EINVAL, "null batch");
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(lbm_batch* out, const lbm_params* params, int count)
+{
+    if (!out) return fail(LBM_EINVAL, "null output");
+    *out = nullptr;
+    if (!params || count < 1 || count > 65535) return fail(LBM_EINVAL, "count must be in [1, 65535]");
+    for (int i = 0; i < count; ++i) {
+        if (params[i].storage != LBM_FP32)
+            return fail(LBM_EUNSUPPORTED, "batched instances use FP32 storage (instance %d)", i);
+        if (params[i].pair != LBM_D3Q27_D3Q19 && params[i].pair != LBM_D3Q19_D3Q7)
+            return fail(LBM_EUNSUPPORTED, "batched instances use D3Q27xD3Q19 or D3Q19xD3Q7 (instance %d)", i);
+    }
+    lbm_batch_ctx* b = new (std::nothrow) lbm_batch_ctx();
+    if (!b) return fail(LBM_ENOMEM, "host allocation failed");
+    int rc = LBM_OK;
+    cudaGetDevice(&b->device);
+    cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return fail(LBM_ECUDA, "stream creation failed");
+    }
+    b->own_stream = true;
+    for (int i = 0; i < count && rc == LBM_OK; ++i) {
+        lbm_handle h = nullptr;
+        rc = lbm_create_params(&h, &params[i]);
+        if (rc) break;
+        b->inst.push_back(h);
+        if ((rc = lbm_set_stream(h, b->stream))) break;
+        if ((rc = ensure_store(h))) break;
+    }
+    if (rc == LBM_OK && (cudaMalloc(&b->d_sync, 4 * sizeof(unsigned)) != cudaSuccess ||
+                         cudaMemset(b->d_sync, 0, 4 * sizeof(unsigned)) != cudaSuccess)) {
+        cudaGetLastError();
+        rc = fail(LBM_ENOMEM, "batch barrier allocation failed");
+    }
+    if (rc == LBM_OK) rc = batch_build_tiles(b);
+    if (rc) {
+        std::string msg = g_last_error;
+        lbm_batch_destroy(b);
+        g_last_error = msg;
+        return rc;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_count(lbm_batch b, int* count)
+{
+    if (!b || !count) return fail(LBM_EINVAL, "null argument");
+    *count = (int)b->inst.size();
+    return LBM_OK;
+}
+
+int lbm_batch_instance(lbm_batch b, int i, lbm_handle* h)
+{
+    if (!b || !h) return fail(LBM_EINVAL, "null argument");
+    if (i < 0 || i >= (int)b->inst.size()) return fail(LBM_EINVAL, "instance %d out of range", i);
+    *h = b->inst[i];
+    return LBM_OK;
+}
+
+int lbm_batch_set_stream(lbm_batch b, void* stream)
+{
+    int rc = batch_check(b);
+    if (rc) return rc;
+    if (b->own_stream) {
+        cudaStreamSynchronize(b->stream);
+        cudaStreamDestroy(b->stream);
+    }
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->own_stream = false;
+    for (lbm_ctx* h : b->inst) h->stream = b->stream;
+    batch_drop_graph(b);
+    return LBM_OK;
+}
+
+int lbm_batch_set_mode(lbm_batch b, int mode, int steps_per_launch)
+{
+    if (!b) return fail(LBM_EINVAL, "null batch");
+    if (mode != LBM_BATCH_PERSISTENT && mode != LBM_BATCH_PER_STEP) return fail(LBM_EINVAL, "unknown mode %d", mode);
+    if (steps_per_launch < 1) return fail(LBM_EINVAL, "steps per launch must be >= 1");
+    b->mode = mode;
+    b->chunk = steps_per_launch;
+    return LBM_OK;
+}
+
+int lbm_batch_set_block(lbm_batch b, int bx, int by)
+{
+    int rc = batch_check(b);
+    if (rc) return rc;
+    if (!(bx == 16 || bx == 32 || bx == 64 || bx == 128) || by < 1 || bx * by > 256 || (bx * by) % 32 != 0)
+        return fail(LBM_EINVAL, "batch block (%d, %d): bx in {16, 32, 64, 128}, bx*by a multiple of 32 <= 256", bx, by);
+    b->bx = bx;
+    b->by = by;
+    return batch_build_tiles(b);
+}
+
+int lbm_batch_get_config(lbm_batch b, int* bx, int* by, int* mode, int* grid)
+{
+    if (!b) return fail(LBM_EINVAL, "null batch");
+    if (bx) *bx = b->bx;
+    if (by) *by = b->by;
+    if (mode) *mode = b->mode;
+    if (grid) *grid = b->mode == LBM_BATCH_PERSISTENT ? b->persistent_grid : (int)b->ntiles;
+    return LBM_OK;
+}
+
+int lbm_batch_init_tgv(lbm_batch b, uint64_t seed, double noise_amp)
+{
+    int rc = batch_check(b);
+    if (rc) return rc;
+    for (lbm_ctx* h : b->inst)
+        if ((rc = lbm_init_tgv(h, seed, noise_amp))) return rc;
+    b->initialized = true;
+    b->step = 0;
+    b->odd = 0;
+    batch_sync_instances(b);
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch b, int64_t nsteps)
+{
+    int rc = batch_check(b);
+    if (rc) return rc;
+    if (nsteps < 0) return fail(LBM_EINVAL, "negative step count");
+    if (!b->initialized) return fail(LBM_ESTATE, "batch step before initialisation");
+    while (nsteps > 0) {
+        if (b->mode == LBM_BATCH_PERSISTENT) {
+            const int k = (int)(nsteps < b->chunk ? nsteps : b->chunk);
+            LBM_CUDA(batch_launch_persistent(b, k, b->odd, b->stream), "persistent batch launch");
+            b->odd ^= (k & 1);
+            b->step += k;
+            nsteps -= k;
+            continue;
+        }
+        if (b->stream != nullptr && b->odd == 0 && nsteps >= kBatchGraphSteps) {
+            if (!b->graph) {
+                cudaGraph_t g = nullptr;
+                cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    for (int s = 0; s < kBatchGraphSteps && e == cudaSuccess; ++s) e = batch_launch_step(b, s & 1, b->stream);
+                    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+                    if (e == cudaSuccess) e = e2;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+                if (g) cudaGraphDestroy(g);
+                if (e != cudaSuccess) return cuda_fail(e, "batch graph capture");
+            }
+            LBM_CUDA(cudaGraphLaunch(b->graph, b->stream), "batch graph launch");
+            b->step += kBatchGraphSteps;
+            nsteps -= kBatchGraphSteps;
+            continue;
+        }
+        LBM_CUDA(batch_launch_step(b, b->odd, b->stream), "batch step launch");
+        b->odd ^= 1;
+        b->step += 1;
+        nsteps -= 1;
+    }
+    batch_sync_instances(b);
+    return LBM_OK;
+}
+
+int lbm_batch_synchronize(lbm_batch b)
+{
+    int rc = batch_check(b);
+    if (rc) return rc;
+    LBM_CUDA(cudaStreamSynchronize(b->stream), "batch synchronize");
+    unsigned flags[4];
+    LBM_CUDA(cudaMemcpy(flags, b->d_sync, sizeof(flags), cudaMemcpyDeviceToHost), "read barrier state");
+    if (flags[2] != 0u) {
+        cudaMemset(b->d_sync, 0, 4 * sizeof(unsigned));
+        return fail(LBM_ETIMEOUT, "a grid-barrier wait of the persistent batch kernel ran out; "
+                                  "the state of the batch is undefined");
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_diagnostics(lbm_batch b, lbm_diag* out)
+{
+    int rc = lbm_batch_synchronize(b);
+    if (rc) return rc;
+    if (!out) return fail(LBM_EINVAL, "null output");
+    int worst = LBM_OK;
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        rc = lbm_diagnostics(b->inst[i], &out[i]);
+        if (rc == LBM_ENONFINITE) worst = rc;
+        else if (rc) return rc;
+    }
+    return worst;
+}
+
+int lbm_batch_autotune(lbm_batch b, int reps, double* best_ms_per_step)
+{
+    int rc = batch_check(b);
+    if (rc) return rc;
+    if (!b->initialized) return fail(LBM_ESTATE, "autotune needs an initialised batch");
+    if (reps < 1) return fail(LBM_EINVAL, "reps must be >= 1");
+    if ((rc = lbm_batch_synchronize(b))) return rc;
+    std::vector<void*> backup(b->inst.size(), nullptr);
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        if (cudaMalloc(&backup[i], b->inst[i]->store_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            for (void* p : backup) if (p) cudaFree(p);
+            return fail(LBM_ENOMEM, "autotune backup allocation failed");
+        }
+        cudaMemcpyAsync(backup[i], b->inst[i]->store, b->inst[i]->store_bytes, cudaMemcpyDeviceToDevice, b->stream);
+    }
+    static const int cand[][2] = {{16, 8}, {16, 16}, {32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {128, 2}};
+    const int save_bx = b->bx, save_by = b->by, save_mode = b->mode, save_odd = b->odd;
+    const int64_t save_step = b->step;
+    double best = 1e300;
+    int bbx = save_bx, bby = save_by, bmode = save_mode;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (const auto& c : cand) {
+        b->bx = c[0];
+        b->by = c[1];
+        if ((rc = batch_build_tiles(b))) break;
+        for (int mode = 0; mode < 2 && rc == LBM_OK; ++mode) {
+            b->mode = mode;
+            lbm_batch_step(b, 2);
+            cudaEventRecord(e0, b->stream);
+            rc = lbm_batch_step(b, 2 * (int64_t)reps);
+            cudaEventRecord(e1, b->stream);
+            if (rc) break;
+            if ((rc = lbm_batch_synchronize(b))) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double per = ms / (2.0 * reps);
+            if (per < best) {
+                best = per;
+                bbx = c[0];
+                bby = c[1];
+                bmode = mode;
+            }
+        }
+        if (rc) break;
+    }
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        cudaMemcpyAsync(b->inst[i]->store, backup[i], b->inst[i]->store_bytes, cudaMemcpyDeviceToDevice, b->stream);
+    }
+    cudaStreamSynchronize(b->stream);
+    for (void* p : backup) cudaFree(p);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->odd = save_odd;
+    b->step = save_step;
+    b->bx = bbx;
+    b->by = bby;
+    b->mode = bmode;
+    int rc2 = batch_build_tiles(b);
+    batch_sync_instances(b);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    if (best_ms_per_step) *best_ms_per_step = best;
+    return LBM_OK;
+}
+
+int lbm_batch_set_barrier_test(lbm_batch b, unsigned extra_blocks, unsigned spin_limit)
+{
+    if (!b) return fail(LBM_EINVAL, "null batch");
+    if (spin_limit < 1) return fail(LBM_EINVAL, "spin limit must be >= 1");
+    b->extra_blocks = extra_blocks;
+    b->spin_limit = spin_limit;
+    return LBM_OK;
+}
+
+int lbm_batch_destroy(lbm_batch b)
+{
+    if (!b) return LBM_OK;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_drop_graph(b);
+    for (lbm_ctx* h : b->inst) {
+        h->stream = nullptr;
+        h->own_stream = false;
+        lbm_destroy(h);
+    }
+    if (b->d_inst) cudaFree(b->d_inst);
+    if (b->d_tile) cudaFree(b->d_tile);
+    if (b->d_sync) cudaFree(b->d_sync);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
     return LBM_OK;
 }
 

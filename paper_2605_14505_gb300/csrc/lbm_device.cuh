@@ -216,14 +216,22 @@ struct AA {
 
 // Element offsets are 32-bit (slot * n3 + node < 2^32 for every supported
 // size); the 64-bit address is formed at each access.
+#ifndef LBM_ADDR64
+#define LBM_ADDR64 0
+#endif
 template <class L, bool ODD, class T>
 __device__ __forceinline__ void load_node(const T* __restrict__ base, uint32_t n3, const NodeAddr& a,
                                           float* v)
 {
     sfor<0, L::kQ>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
+#if LBM_ADDR64
+        const T* p = base + AA<L, ODD>::template read_off<i>(a);
+        v[i] = ld_pop<T>(p + (size_t)AA<L, ODD>::template read_slot<i>() * n3);
+#else
         v[i] = ld_pop<T>(base + (AA<L, ODD>::template read_slot<i>() * n3 +
                                  AA<L, ODD>::template read_off<i>(a)));
+#endif
     });
 }
 
@@ -233,9 +241,14 @@ __device__ __forceinline__ void store_node(T* __restrict__ base, uint32_t n3, co
 {
     sfor<0, L::kQ>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
+#if LBM_ADDR64
+        T* p = base + AA<L, ODD>::template write_off<i>(a);
+        st_pop<T>(p + (size_t)AA<L, ODD>::template write_slot<i>() * n3, v[i]);
+#else
         st_pop<T>(base + (AA<L, ODD>::template write_slot<i>() * n3 +
                           AA<L, ODD>::template write_off<i>(a)),
                   v[i]);
+#endif
     });
 }
 

@@ -13,8 +13,28 @@ struct StepArgs {
     Phys ph;
 };
 
-// One fused AA step for every node: load the QF + QG populations (coalesced
+// The fused AA update of one node: load the QF + QG populations (coalesced
 // along x), moments, coupled rho'/u solve, f and g collisions, store.
+template <class P, int FORCING, class T, bool ODD>
+__device__ __forceinline__ void update_node(void* fv, void* gv, const Geometry& geo, const Phys& ph, int x,
+                                            int y, int z)
+{
+    const NodeAddr a(geo, x, y, z);
+    T* __restrict__ f = static_cast<T*>(fv);
+    T* __restrict__ g = static_cast<T*>(gv);
+    const uint32_t n3 = geo.n3;
+    float h[P::QF], k[P::QG];
+    load_node<typename P::LF, ODD, T>(f, n3, a, h);
+    load_node<typename P::LG, ODD, T>(g, n3, a, k);
+    const Macro m = node_macro<P>(h, k, ph);
+    collide_f<P, FORCING>(h, m, ph);
+    collide_g<P>(k, m, ph);
+    const NodeAddr b(geo, (int)launder(x), (int)launder(y), (int)launder(z));
+    store_node<typename P::LF, ODD, T>(f, n3, b, h);
+    store_node<typename P::LG, ODD, T>(g, n3, b, k);
+}
+
+// One AA step for every node of one lattice.
 template <class P, int FORCING, class T, bool ODD>
 __global__ void __launch_bounds__(256) k_step(StepArgs args)
 {
@@ -22,20 +42,30 @@ __global__ void __launch_bounds__(256) k_step(StepArgs args)
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= args.geo.nx || y >= args.geo.ny) return;
-    const NodeAddr a(args.geo, x, y, z);
-    T* __restrict__ f = static_cast<T*>(args.f);
-    T* __restrict__ g = static_cast<T*>(args.g);
-    const uint32_t n3 = args.geo.n3;
-    float h[P::QF], k[P::QG];
-    load_node<typename P::LF, ODD, T>(f, n3, a, h);
-    load_node<typename P::LG, ODD, T>(g, n3, a, k);
-    const Macro m = node_macro<P>(h, k, args.ph);
-    collide_f<P, FORCING>(h, m, args.ph);
-    collide_g<P>(k, m, args.ph);
-    const NodeAddr b(args.geo, (int)launder(x), (int)launder(y), (int)launder(z));
-    store_node<typename P::LF, ODD, T>(f, n3, b, h);
-    store_node<typename P::LG, ODD, T>(g, n3, b, k);
+    update_node<P, FORCING, T, ODD>(args.f, args.g, args.geo, args.ph, x, y, z);
 }
+
+// Batched update: per-instance descriptor and launch arguments.
+struct BatchInstance {
+    void* f;
+    void* g;
+    Geometry geo;
+    Phys ph;
+    int variant;      // 4 * (0: D3Q27xD3Q19, 1: D3Q19xD3Q7) + forcing
+    uint32_t tile0;   // first tile of this instance in the global tile list
+    uint32_t tx, ty;  // tiles along x and y of one z-plane
+};
+
+struct BatchArgs {
+    const BatchInstance* inst;
+    const uint16_t* tile_inst;  // instance index of every tile
+    uint32_t ntiles;
+    int steps;                  // time steps of one persistent launch
+    int odd0;                   // AA layout parity at the start
+    unsigned* sync;             // grid barrier: arrivals, generation, error flag
+    unsigned nblocks;           // blocks that must arrive at each barrier
+    unsigned spin_limit;        // polls before a barrier wait gives up
+};
 
 __device__ __forceinline__ void node_xyz(const Geometry& geo, uint32_t idx, int& x, int& y, int& z)
 {

@@ -104,7 +104,22 @@ _SIGS = {
     "lbm_autotune": ([_H, ctypes.c_int, _DP], ctypes.c_int),
     "lbm_set_graphs": ([_H, ctypes.c_int], ctypes.c_int),
     "lbm_destroy": ([_H], ctypes.c_int),
+    "lbm_batch_create": ([ctypes.POINTER(_H), ctypes.POINTER(lbm_params), ctypes.c_int], ctypes.c_int),
+    "lbm_batch_count": ([_H, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "lbm_batch_instance": ([_H, ctypes.c_int, ctypes.POINTER(_H)], ctypes.c_int),
+    "lbm_batch_set_stream": ([_H, ctypes.c_void_p], ctypes.c_int),
+    "lbm_batch_set_mode": ([_H, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "lbm_batch_set_block": ([_H, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "lbm_batch_get_config": ([_H] + [ctypes.POINTER(ctypes.c_int)] * 4, ctypes.c_int),
+    "lbm_batch_init_tgv": ([_H, ctypes.c_uint64, ctypes.c_double], ctypes.c_int),
+    "lbm_batch_step": ([_H, ctypes.c_int64], ctypes.c_int),
+    "lbm_batch_synchronize": ([_H], ctypes.c_int),
+    "lbm_batch_diagnostics": ([_H, ctypes.POINTER(lbm_diag)], ctypes.c_int),
+    "lbm_batch_autotune": ([_H, ctypes.c_int, _DP], ctypes.c_int),
+    "lbm_batch_set_barrier_test": ([_H, ctypes.c_uint, ctypes.c_uint], ctypes.c_int),
+    "lbm_batch_destroy": ([_H], ctypes.c_int),
 }
+BATCH_MODES = {"persistent": 0, "per_step": 1}
 
 _lib = None
 
@@ -387,3 +402,76 @@ class Simulation:
 
     def velocity_sets(self):
         return lbm_velocity_set(self.qf), lbm_velocity_set(self.qg)
+
+
+# ---- batched instances -------------------------------------------------------
+
+def lbm_batch_create(params_list) -> ctypes.c_void_p:
+    arr = (lbm_params * len(params_list))(*params_list)
+    b = _H()
+    _check(load_library().lbm_batch_create(ctypes.byref(b), arr, len(params_list)))
+    return b
+
+
+def lbm_batch_count(b) -> int:
+    c = ctypes.c_int()
+    _check(load_library().lbm_batch_count(b, ctypes.byref(c)))
+    return c.value
+
+
+def lbm_batch_instance(b, i: int) -> ctypes.c_void_p:
+    h = _H()
+    _check(load_library().lbm_batch_instance(b, i, ctypes.byref(h)))
+    return h
+
+
+def lbm_batch_set_stream(b, stream_ptr: int):
+    _check(load_library().lbm_batch_set_stream(b, ctypes.c_void_p(stream_ptr)))
+
+
+def lbm_batch_set_mode(b, mode, steps_per_launch: int = 100):
+    _check(load_library().lbm_batch_set_mode(b, _enum(mode, BATCH_MODES), steps_per_launch))
+
+
+def lbm_batch_set_block(b, bx: int, by: int):
+    _check(load_library().lbm_batch_set_block(b, bx, by))
+
+
+def lbm_batch_get_config(b) -> dict:
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(load_library().lbm_batch_get_config(b, *[ctypes.byref(x) for x in v]))
+    return {"bx": v[0].value, "by": v[1].value, "mode": v[2].value, "grid": v[3].value}
+
+
+def lbm_batch_init_tgv(b, seed: int = 0, noise_amp: float = 0.0):
+    _check(load_library().lbm_batch_init_tgv(b, seed, noise_amp))
+
+
+def lbm_batch_step(b, nsteps: int):
+    _check(load_library().lbm_batch_step(b, int(nsteps)))
+
+
+def lbm_batch_synchronize(b):
+    _check(load_library().lbm_batch_synchronize(b))
+
+
+def lbm_batch_diagnostics(b) -> list:
+    n = lbm_batch_count(b)
+    out = (lbm_diag * n)()
+    _check(load_library().lbm_batch_diagnostics(b, out))
+    return [d.as_dict() for d in out]
+
+
+def lbm_batch_autotune(b, reps: int = 3) -> float:
+    ms = ctypes.c_double()
+    _check(load_library().lbm_batch_autotune(b, reps, ctypes.byref(ms)))
+    return ms.value
+
+
+def lbm_batch_set_barrier_test(b, extra_blocks: int, spin_limit: int):
+    _check(load_library().lbm_batch_set_barrier_test(b, extra_blocks, spin_limit))
+
+
+def lbm_batch_destroy(b):
+    if b:
+        _check(load_library().lbm_batch_destroy(b))
