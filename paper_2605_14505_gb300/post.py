@@ -1,0 +1,76 @@
+"""Post-processing of the diagnostics time series (paper Sections 3.3-3.5).
+
+These are host-side reductions of a few numbers per sample, not part of the
+GPU update. Lattice-unit diagnostics (lbm_diag) are converted to the paper's
+units with U = L = 1: time t = step * U0 / L_LB, energies / U0^2,
+dissipation rates * L_LB / U0^3, where L_LB = n / (2 pi).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_trapezoid = getattr(np, "trapezoid", None) or np.trapz
+
+
+def to_physical(series, U0: float, L: float) -> dict:
+    """Convert a list of lbm_diag dicts to arrays in the paper's units."""
+    step = np.array([d["step"] for d in series], dtype=np.float64)
+    out = {"t": step * U0 / L}
+    for key in ("Ek", "Ep"):
+        out[key] = np.array([d[key] for d in series]) / U0 ** 2
+    for key in ("eps_k", "eps_p", "eps_k_curl"):
+        out[key] = np.array([d[key] for d in series]) * L / U0 ** 3
+    out["Etot"] = out["Ek"] + out["Ep"]          # Eq. 24
+    return out
+
+
+def total_dissipation_rate(t, Etot):
+    """-dE_tot/dt by second-order central differences on a uniform time grid
+    (one-sided second-order differences at the two ends), Sections 3.1, 3.3."""
+    t = np.asarray(t, dtype=np.float64)
+    E = np.asarray(Etot, dtype=np.float64)
+    if len(t) < 3:
+        raise ValueError("need at least three samples")
+    return -np.gradient(E, t, edge_order=2)
+
+
+def buoyancy_reynolds(eps_k, Re: float, Fr: float):
+    """Eq. 27, R = eps_k / (nu N^2), with nu = 1/Re and N = 1/Fr (U = L = 1)."""
+    return np.asarray(eps_k, dtype=np.float64) * Re * Fr ** 2
+
+
+def flux_coefficient(eps_p, eps_k):
+    """Gamma = eps_p / eps_k (Section 3.5)."""
+    return np.asarray(eps_p, dtype=np.float64) / np.asarray(eps_k, dtype=np.float64)
+
+
+def _integral(t, y, t_end):
+    t = np.asarray(t, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    m = t <= t_end + 1e-12
+    return _trapezoid(y[m], t[m])
+
+
+def bulk_flux_coefficient(t, eps_p, eps_k, t_end: float = 30.0):
+    """Eq. 28: Gamma_b = int_0^T eps_p dt / int_0^T eps_k dt (trapezoidal rule)."""
+    return _integral(t, eps_p, t_end) / _integral(t, eps_k, t_end)
+
+
+def turbulent_froude(t, eps_k, Ek, Fr: float, t_end: float = 30.0):
+    """Eq. 29: Fr_t = int_0^T eps_k dt / (N int_0^T E_k dt), N = 1/Fr."""
+    return _integral(t, eps_k, t_end) / ((1.0 / Fr) * _integral(t, Ek, t_end))
+
+
+def energy_spectrum(u, n: int):
+    """Shell-averaged kinetic-energy spectrum E(k) of a periodic velocity field
+    u (3 x n^3, x fastest, any units) on [0, 2 pi)^3 (Section 3.5): the energy
+    of all Fourier modes with round(|k|) = k, normalised so that
+    sum_k E(k) = <|u|^2> / 2. Returns (k, E)."""
+    u = np.asarray(u, dtype=np.float64).reshape(3, n, n, n)
+    uh = np.fft.fftn(u, axes=(1, 2, 3)) / n ** 3
+    e = 0.5 * np.sum(np.abs(uh) ** 2, axis=0)
+    kk = np.fft.fftfreq(n, d=1.0 / n)
+    KZ, KY, KX = np.meshgrid(kk, kk, kk, indexing="ij")
+    shell = np.rint(np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2)).astype(np.int64)
+    E = np.bincount(shell.ravel(), weights=e.ravel())
+    return np.arange(len(E)), E
