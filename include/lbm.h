@@ -232,7 +232,8 @@ int lbm_step_count(lbm_handle h, int64_t* step);
 int lbm_diagnostics_noalloc(lbm_handle h, lbm_diag* out);
 
 /* Launch shape of the step kernel (threads along x and y; bx * by <= 256,
- * bx a multiple of 32). */
+ * bx a multiple of 32). With two nodes per thread (lbm_set_pairing) a
+ * thread along x covers two nodes. */
 int lbm_set_block(lbm_handle h, int bx, int by);
 int lbm_get_block(lbm_handle h, int* bx, int* by);
 
@@ -240,6 +241,13 @@ int lbm_get_block(lbm_handle h, int* bx, int* by);
  * each, CUDA events) and keep the fastest. The state is saved and restored,
  * so the simulation is unchanged. best_ms_per_step may be NULL. */
 int lbm_autotune(lbm_handle h, int reps, double* best_ms_per_step);
+
+/* For FP16/BF16 storage and even nx the step kernel updates two x-adjacent
+ * nodes per thread, moving each pair's values of a slot as one 32-bit word
+ * where the AA access keeps them aligned; the per-node arithmetic is the
+ * same. enable = 0 selects the one-node-per-thread kernel (default 1). Resets
+ * the launch shape to its default. */
+int lbm_set_pairing(lbm_handle h, int enable);
 
 /* Enable (1, default) or disable (0) CUDA-graph replay in lbm_step. */
 int lbm_set_graphs(lbm_handle h, int enable);

@@ -81,6 +81,7 @@ struct lbm_ctx {
     int64_t step = 0;
     int odd = 0;           // layout parity of the store
     int bx = 0, by = 0;
+    bool pairing = true;   // two nodes per thread where a kernel exists (16-bit storage, even nx)
     // diagnostics scratch
     float* diag_fields = nullptr;
     double* diag_partials = nullptr;
@@ -119,9 +120,15 @@ void derive_phys(lbm_ctx* h)
     h->geo.n3 = (uint32_t)((size_t)p.nx * p.ny * p.nz);
 }
 
+bool uses_pairs(const lbm_ctx* h)
+{
+    return h->pairing && h->ks->step2[h->p.forcing][0] != nullptr && (h->p.nx % 2) == 0;
+}
+
 void default_block(lbm_ctx* h)
 {
-    int bx = h->p.nx >= 128 ? 128 : (h->p.nx >= 64 ? 64 : 32);
+    const int xunits = uses_pairs(h) ? h->p.nx / 2 : h->p.nx;
+    int bx = xunits >= 128 ? 128 : (xunits >= 64 ? 64 : 32);
     int by = 256 / bx;
     while (by > 1 && by / 2 >= h->p.ny) by /= 2;
     h->bx = bx;
@@ -190,7 +197,8 @@ int ensure_diag(lbm_ctx* h)
 
 dim3 step_grid(const lbm_ctx* h)
 {
-    return dim3((unsigned)((h->p.nx + h->bx - 1) / h->bx), (unsigned)((h->p.ny + h->by - 1) / h->by),
+    const int xunits = uses_pairs(h) ? h->p.nx / 2 : h->p.nx;
+    return dim3((unsigned)((xunits + h->bx - 1) / h->bx), (unsigned)((h->p.ny + h->by - 1) / h->by),
                 (unsigned)h->p.nz);
 }
 
@@ -202,7 +210,8 @@ cudaError_t launch_step(lbm_ctx* h, int odd, cudaStream_t s)
     a.geo = h->geo;
     a.ph = h->ph;
     void* args[] = {&a};
-    return cudaLaunchKernel(h->ks->step[h->p.forcing][odd], step_grid(h), dim3(h->bx, h->by), args, 0, s);
+    const void* k = uses_pairs(h) ? h->ks->step2[h->p.forcing][odd] : h->ks->step[h->p.forcing][odd];
+    return cudaLaunchKernel(k, step_grid(h), dim3(h->bx, h->by), args, 0, s);
 }
 
 int flat_grid(const lbm_ctx* h)
@@ -371,6 +380,7 @@ int lbm_set_storage(lbm_handle h, int storage)
     if (!ks) return fail(LBM_EUNSUPPORTED, "storage %d is not compiled in for pair %d", storage, h->p.pair);
     h->p.storage = storage;
     h->ks = ks;
+    default_block(h);
     drop_graph(h);
     return LBM_OK;
 }
@@ -786,6 +796,15 @@ int lbm_autotune(lbm_handle h, int reps, double* best_ms_per_step)
     h->by = bby;
     drop_graph(h);
     if (best_ms_per_step) *best_ms_per_step = best;
+    return LBM_OK;
+}
+
+int lbm_set_pairing(lbm_handle h, int enable)
+{
+    if (!h) return fail(LBM_EINVAL, "null handle");
+    h->pairing = enable != 0;
+    default_block(h);
+    drop_graph(h);
     return LBM_OK;
 }
 

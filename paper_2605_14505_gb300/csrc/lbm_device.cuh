@@ -301,9 +301,13 @@ LBM_HD float e_dot(float ux, float uy, float uz)
     return eu;
 }
 
-// Moments of one node. On return each opposite pair (2m-1, 2m) of h and k
-// holds its sum and difference, the form the collisions take.
-template <class P>
+// Moments of one node. EXACT (FP32 storage): on return each opposite pair
+// (2m-1, 2m) of h and k holds its sum and difference, the form the exact
+// collisions take, and rho, 1/rho enter only through their deviations from 1.
+// !EXACT (16-bit storage, whose rounding of ~5e-4 per step dwarfs the 1e-8
+// effects the exact forms remove): h and k are left as they are and the
+// plain reciprocal is used.
+template <class P, bool EXACT = true>
 LBM_HD Macro node_macro(float* h, float* k, const Phys& ph)
 {
     using LF = typename P::LF;
@@ -314,8 +318,10 @@ LBM_HD Macro node_macro(float* h, float* k, const Phys& ph)
         constexpr int i = 2 * decltype(mc)::value + 1;
         const float sum = h[i] + h[i + 1];
         const float dif = h[i] - h[i + 1];
-        h[i] = sum;       // pair form, see collide_f
-        h[i + 1] = dif;
+        if constexpr (EXACT) {
+            h[i] = sum;       // pair form, see collide_f
+            h[i + 1] = dif;
+        }
         drho += sum;
         if constexpr (LF::ex(i) == 1) jx += dif;
         if constexpr (LF::ex(i) == -1) jx -= dif;
@@ -327,17 +333,29 @@ LBM_HD Macro node_macro(float* h, float* k, const Phys& ph)
     sfor<0, kPairs<LG>>([&](auto mc) {
         constexpr int i = 2 * decltype(mc)::value + 1;
         const float sum = k[i] + k[i + 1];
-        const float dif = k[i] - k[i + 1];
-        k[i] = sum;
-        k[i + 1] = dif;
+        if constexpr (EXACT) {
+            k[i + 1] = k[i] - k[i + 1];
+            k[i] = sum;
+        }
         a += sum;
     });
     m.drho = drho;
+    m.jx = jx; m.jy = jy; m.jz = jz;
+    m.a = a;
+    if constexpr (!EXACT) {
+        m.rho = 1.f + drho;
+        m.irho = 1.f / m.rho;
+        m.dirho = m.irho - 1.f;
+        m.rho_p = (a + ph.kappa * jz * m.irho) / (1.f + 0.5f * ph.kappa * ph.G * m.irho);
+        m.Fz = -ph.G * m.rho_p;
+        m.ux = jx * m.irho;
+        m.uy = jy * m.irho;
+        m.uz = (jz + 0.5f * m.Fz) * m.irho;
+        return m;
+    }
     m.dirho = -drho / (1.f + drho);
     m.rho = 1.f + drho;
     m.irho = 1.f + m.dirho;
-    m.jx = jx; m.jy = jy; m.jz = jz;
-    m.a = a;
     // rho' = a + kappa * u_z with u_z = (j_z - G rho' / 2) / rho  (Eqs. 7, 12, 16-18),
     // solved in closed form.
     // num / (1 + x) with x = kappa G / (2 rho) ~ 1e-6: 1 + x rounded in FP32
@@ -366,7 +384,7 @@ LBM_HD float bgk(float f, float feq, float dl)
 // f_eq = w (base + rho (e.u)^2 / (2 cs^4)) +- w rho e.u / cs^2, base = drho - rho u^2 / (2 cs^2).
 //
 // f collision (Eqs. 5, 8, 9) with the forcing scheme, in place on h.
-template <class P, int FORCING>
+template <class P, int FORCING, bool EXACT = true>
 LBM_HD void collide_f(float* h, const Macro& m, const Phys& ph)
 {
     using LF = typename P::LF;
@@ -440,29 +458,41 @@ LBM_HD void collide_f(float* h, const Macro& m, const Phys& ph)
             Fs = w * fmaf(m.drho, ps, ps);
             Fa = (ez != 0) ? w * c1 * (float)ez * m.Fz : 0.f;     // w rho e_z du / cs^2
         }
-        // Even and odd parts relax separately: forming hs +- ha first would round
-        // the even part (density, stress) to the ulp of the much larger odd part.
-        const float sp = bgk(h[i], 2.f * hs, dl) + 2.f * Fs;   // h_i + h_j
-        const float dp = bgk(h[j], 2.f * ha, dl) + 2.f * Fa;   // h_i - h_j
-        h[i] = 0.5f * (sp + dp);
-        h[j] = 0.5f * (sp - dp);
+        if constexpr (EXACT) {
+            // Even and odd parts relax separately: forming hs +- ha first would round
+            // the even part (density, stress) to the ulp of the much larger odd part.
+            const float sp = bgk(h[i], 2.f * hs, dl) + 2.f * Fs;   // h_i + h_j
+            const float dp = bgk(h[j], 2.f * ha, dl) + 2.f * Fa;   // h_i - h_j
+            h[i] = 0.5f * (sp + dp);
+            h[j] = 0.5f * (sp - dp);
+        } else {
+            h[i] = bgk(h[i], hs + ha, dl) + (Fs + Fa);
+            h[j] = bgk(h[j], hs - ha, dl) + (Fs - Fa);
+        }
     };
-    sfor<3, kPairs<LF>>([&](auto mc) {
-        constexpr int i = 2 * decltype(mc)::value + 1;
-        const float ha = LF::w(i) * c1 * e_dot<LF, i>(mx, my, mz);
-        if constexpr (LF::ex(i) != 0) ox += (float)LF::ex(i) * ha;
-        if constexpr (LF::ey(i) != 0) oy += (float)LF::ey(i) * ha;
-        if constexpr (LF::ez(i) != 0) oz += (float)LF::ez(i) * ha;
-        relax_pair(mc, ha);
-    });
-    relax_pair(std::integral_constant<int, 0>{}, fmaf(0.5f, mx, -ox));   // slots 1, 2: +-x
-    relax_pair(std::integral_constant<int, 1>{}, fmaf(0.5f, my, -oy));   // slots 3, 4: +-y
-    relax_pair(std::integral_constant<int, 2>{}, fmaf(0.5f, mz, -oz));   // slots 5, 6: +-z
+    if constexpr (EXACT) {
+        sfor<3, kPairs<LF>>([&](auto mc) {
+            constexpr int i = 2 * decltype(mc)::value + 1;
+            const float ha = LF::w(i) * c1 * e_dot<LF, i>(mx, my, mz);
+            if constexpr (LF::ex(i) != 0) ox += (float)LF::ex(i) * ha;
+            if constexpr (LF::ey(i) != 0) oy += (float)LF::ey(i) * ha;
+            if constexpr (LF::ez(i) != 0) oz += (float)LF::ez(i) * ha;
+            relax_pair(mc, ha);
+        });
+        relax_pair(std::integral_constant<int, 0>{}, fmaf(0.5f, mx, -ox));   // slots 1, 2: +-x
+        relax_pair(std::integral_constant<int, 1>{}, fmaf(0.5f, my, -oy));   // slots 3, 4: +-y
+        relax_pair(std::integral_constant<int, 2>{}, fmaf(0.5f, mz, -oz));   // slots 5, 6: +-z
+    } else {
+        sfor<0, kPairs<LF>>([&](auto mc) {
+            constexpr int i = 2 * decltype(mc)::value + 1;
+            relax_pair(mc, LF::w(i) * c1 * e_dot<LF, i>(mx, my, mz));
+        });
+    }
 }
 
 // g collision (Eqs. 11, 12, 14, 15): g_eq = (rho' + rho0) Theta(u), S_i = w_i (-u_z beta).
 // For deviations: g_eq_i - w_i rho0 = w_i (rho' + (rho' + rho0) P_i).
-template <class P>
+template <class P, bool EXACT = true>
 LBM_HD void collide_g(float* k, const Macro& m, const Phys& ph)
 {
     using LG = typename P::LG;
@@ -482,10 +512,16 @@ LBM_HD void collide_g(float* k, const Macro& m, const Phys& ph)
         const float eu = e_dot<LG, i>(m.ux, m.uy, m.uz);
         const float ks = w * fmaf(rr * c2, eu * eu, base);
         const float ka = w * rr * c1 * eu;
-        const float sp = bgk(k[i], 2.f * ks, dl) + 2.f * w * src;
-        const float dp = bgk(k[i + 1], 2.f * ka, dl);
-        k[i] = 0.5f * (sp + dp);
-        k[i + 1] = 0.5f * (sp - dp);
+        if constexpr (EXACT) {
+            const float sp = bgk(k[i], 2.f * ks, dl) + 2.f * w * src;
+            const float dp = bgk(k[i + 1], 2.f * ka, dl);
+            k[i] = 0.5f * (sp + dp);
+            k[i + 1] = 0.5f * (sp - dp);
+        } else {
+            const float si = w * src;
+            k[i] = bgk(k[i], ks + ka, dl) + si;
+            k[i + 1] = bgk(k[i + 1], ks - ka, dl) + si;
+        }
     });
 }
 

@@ -5,6 +5,20 @@
 #include "lbm_kernels.cuh"
 
 #define LBM_STEP_PAIR(P, F, T) {(const void*)k_step<P, F, T, false>, (const void*)k_step<P, F, T, true>}
+#define LBM_STEP2_PAIR(P, F, T) {lbm::step2_ptr<P, F, T, false>(), lbm::step2_ptr<P, F, T, true>()}
+
+namespace lbm {
+// Two-nodes-per-thread kernel for 16-bit storage; FP32 tables hold null (and
+// never instantiate it).
+template <class P, int F, class T, bool ODD>
+inline const void* step2_ptr()
+{
+    if constexpr (std::is_same<T, float>::value)
+        return nullptr;
+    else
+        return (const void*)k_step2<P, F, T, ODD>;
+}
+}  // namespace lbm
 
 #define LBM_DEFINE_KERNEL_SET(NAME, QF_, QG_, T)                                                   \
     namespace lbm {                                                                               \
@@ -16,6 +30,8 @@
             QG_,                                                                                  \
             {LBM_STEP_PAIR(P, 0, T), LBM_STEP_PAIR(P, 1, T), LBM_STEP_PAIR(P, 2, T),              \
              LBM_STEP_PAIR(P, 3, T)},                                                             \
+            {LBM_STEP2_PAIR(P, 0, T), LBM_STEP2_PAIR(P, 1, T), LBM_STEP2_PAIR(P, 2, T),           \
+             LBM_STEP2_PAIR(P, 3, T)},                                                            \
             (const void*)k_init_fields<P, T>,                                                     \
             (const void*)k_init_tgv<P, T>,                                                        \
             (const void*)k_get_pops<P, T>,                                                        \

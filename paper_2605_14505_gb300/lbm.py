@@ -103,6 +103,7 @@ _SIGS = {
     "lbm_get_block": ([_H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "lbm_autotune": ([_H, ctypes.c_int, _DP], ctypes.c_int),
     "lbm_set_graphs": ([_H, ctypes.c_int], ctypes.c_int),
+    "lbm_set_pairing": ([_H, ctypes.c_int], ctypes.c_int),
     "lbm_destroy": ([_H], ctypes.c_int),
     "lbm_batch_create": ([ctypes.POINTER(_H), ctypes.POINTER(lbm_params), ctypes.c_int], ctypes.c_int),
     "lbm_batch_count": ([_H, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -313,6 +314,10 @@ def lbm_autotune(h, reps: int = 3) -> float:
     ms = ctypes.c_double()
     _check(load_library().lbm_autotune(h, reps, ctypes.byref(ms)))
     return ms.value
+
+
+def lbm_set_pairing(h, enable: bool):
+    _check(load_library().lbm_set_pairing(h, 1 if enable else 0))
 
 
 def lbm_set_graphs(h, enable: bool):

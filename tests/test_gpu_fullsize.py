@@ -104,7 +104,7 @@ def test_sampled_parity_full_size(n, pair, forcing, Re, Fr, storage):
     nodes = _sample_nodes(n, 160, seed=n)
     w_even = _check_one_step(sim, p, nodes, STORE_REL[storage], STORE_ABS[storage])   # even -> odd
     w_odd = _check_one_step(sim, p, nodes, STORE_REL[storage], STORE_ABS[storage])    # odd -> even
-    assert max(w_even, w_odd) < 1e-3
+    assert max(w_even, w_odd) < {"fp32": 1e-5, "fp16": 1e-3, "bf16": 8e-3}[storage]
     sim.close()
 
 

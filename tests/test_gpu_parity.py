@@ -249,3 +249,75 @@ def test_checkpoint_roundtrip():
     fa, ga = a.populations()
     fb, gb = b.populations()
     assert np.max(np.abs(fa - fb)) == 0.0 and np.max(np.abs(ga - gb)) == 0.0
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+@pytest.mark.parametrize("shape", [(2, 3, 2), (34, 6, 4), (64, 5, 3), (258, 2, 2)])
+def test_pair_kernel_matches_single_node_kernel(storage, shape):
+    """16-bit storage with even nx runs two nodes per thread; the per-node
+    arithmetic is the one-node kernel's, so both agree to the storage
+    rounding (nx = 2 makes x0 - 1 and x0 + 2 wrap onto the pair itself)."""
+    N = 3e-3
+    p = lattice_params(*shape, "27x19", "sc", 0.55, 0.6, N * LAM, -N / LAM)
+    n3 = shape[0] * shape[1] * shape[2]
+    rho, u, rp = I.random_fields(*shape, 9, 0.05, 0.01, 0.02 / LAM)
+    xf, xg = I.neq_noise(n3, 10), I.neq_noise(n3, 11)
+    a = gpu_sim(p, storage)
+    b = gpu_sim(p, storage)
+    lbm.lbm_set_pairing(b.h, False)
+    for s in (a, b):
+        s.init_fields(rho, u, rp, xf, xg, 1e-3)
+    for _ in range(3):  # odd, even, odd layouts
+        a.step(1)
+        b.step(1)
+        fa, ga = a.populations()
+        fb, gb = b.populations()
+        _, wf, _ = lbm.lbm_velocity_set(27)
+        rel = 2.0 ** -9 if storage == "fp16" else 2.0 ** -6
+        assert np.all(np.abs(fa - fb) <= rel * np.abs(fb - wf[:, None]) + 1e-7)
+        assert np.all(np.abs(ga - gb) <= rel * np.abs(gb) + 1e-7)
+
+
+@pytest.mark.parametrize("forcing", ["guo", "sc", "edm", "hcz"])
+def test_fp16_pair_kernel_against_oracle(forcing):
+    """FP16 deviation storage, pair kernel, one and two steps against the
+    oracle started from the same (FP16-representable) populations."""
+    N = 3e-3
+    p = lattice_params(40, 12, 6, "27x19", forcing, 0.53, 0.56, N * LAM, -N / LAM)
+    g = gpu_sim(p, "fp16")
+    rho, u, rp = I.random_fields(40, 12, 6, 3, 0.05, 0.01, 0.02 / LAM)
+    g.init_fields(rho, u, rp, I.neq_noise(40 * 12 * 6, 4), I.neq_noise(40 * 12 * 6, 5), 1e-3)
+    o = oracle_for(p)
+    f0, g0 = g.populations()   # exactly what the GPU holds
+    o.set_populations(f0[np.argsort(slot_map(27))], g0[np.argsort(slot_map(19))])
+    for _ in range(2):
+        g.step(1)
+        o.step(1)
+        fg, gg = g.populations()
+        fo, go = o.populations()
+        fo, go = fo[slot_map(27)], go[slot_map(19)]
+        _, wf, _ = lbm.lbm_velocity_set(27)
+        _, wg, _ = lbm.lbm_velocity_set(19)
+        df, dg = fo - wf[:, None], go - p.rho0 * wg[:, None]
+        # FP16 storage rounding (half an ulp, relative 2^-11, per step; the first
+        # step's rounding is mixed into other slots by the second), plus FP32
+        # arithmetic and the FP16 subnormal spacing
+        assert np.max(np.abs(fg - fo)) <= 2.0 ** -10 * np.max(np.abs(df)) + 2.0 ** -23
+        assert np.max(np.abs(gg - go)) <= 2.0 ** -10 * np.max(np.abs(dg)) + 2.0 ** -23
+
+
+@pytest.mark.parametrize("pair", ["27x27", "19x19", "19x15", "15x7", "7x27"])
+@pytest.mark.parametrize("forcing", ["guo", "sc"])
+def test_other_stencil_pairs(pair, forcing):
+    """The paper's other stencil pairs (Sections 3.2-3.3), FP32 storage: one and
+    two steps against the oracle, and the diagnostics of the result."""
+    N = 3e-3
+    p = lattice_params(36, 10, 6, pair, forcing, 0.56, 0.58, N * LAM, -N / LAM)
+    g, o = _random_pair(p, seed=13)
+    for _ in range(2):
+        g.step(1)
+        o.step(1)
+        _compare_pops(g, o, p, 1e-5)
+    dg, do = g.diagnostics(), o.diagnostics()
+    for key in ("Ek", "Ep", "eps_k", "eps_p", "eps_k_curl"):
+        assert abs(dg[key] - do[key]) <= 2e-5 * abs(do[key]) + 1e-14, (key, dg[key], do[key])
