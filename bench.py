@@ -402,8 +402,7 @@ def run_ncu_case(args):
     p = lbm.lbm_params_from_physics(args.ncu_n, args.ncu_n, args.ncu_n, pair, FORCING, RE, FR, PR, U0)
     sim = lbm.Simulation(p, storage=storage)
     lbm.lbm_set_graphs(sim.h, False)
-    if args.ncu_single_node:
-        lbm.lbm_set_pairing(sim.h, False)
+    lbm.lbm_set_pairing(sim.h, args.ncu_pairing)
     sim.init_tgv(seed=1, noise_amp=1e-3)
     sim.step(args.ncu_steps)
     d = sim.diagnostics()
@@ -425,8 +424,8 @@ def main():
                     help="run a small profiling case instead of the benchmark")
     ap.add_argument("--ncu-n", type=int, default=128)
     ap.add_argument("--ncu-steps", type=int, default=6)
-    ap.add_argument("--ncu-single-node", action="store_true",
-                    help="profiling case: one node per thread also for 16-bit storage")
+    ap.add_argument("--ncu-pairing", choices=["off", "all", "even"], default="even",
+                    help="profiling case: nodes per thread for 16-bit storage (lbm_set_pairing)")
     args = ap.parse_args()
     if args.ncu_case:
         run_ncu_case(args)

@@ -242,12 +242,17 @@ int lbm_get_block(lbm_handle h, int* bx, int* by);
  * so the simulation is unchanged. best_ms_per_step may be NULL. */
 int lbm_autotune(lbm_handle h, int reps, double* best_ms_per_step);
 
-/* For FP16/BF16 storage and even nx the step kernel updates two x-adjacent
- * nodes per thread, moving each pair's values of a slot as one 32-bit word
- * where the AA access keeps them aligned; the per-node arithmetic is the
- * same. enable = 0 selects the one-node-per-thread kernel (default 1). Resets
- * the launch shape to its default. */
-int lbm_set_pairing(lbm_handle h, int enable);
+/* For FP16/BF16 storage and even nx the step kernel can update two
+ * x-adjacent nodes per thread, moving each pair's values of a slot as one
+ * 32-bit word where the AA access keeps them aligned; the per-node arithmetic
+ * is the same, so the results are bitwise those of the one-node kernel.
+ * mode: LBM_PAIRING_OFF (one node per thread), LBM_PAIRING_ALL (two nodes per
+ * thread at both AA parities), LBM_PAIRING_EVEN (the default: two nodes on
+ * even steps, whose accesses are all aligned, one node on odd steps).
+ * Ignored for FP32 storage and odd nx. Resets the launch shape to its
+ * default. Error: LBM_EINVAL for another mode. */
+enum lbm_pairing { LBM_PAIRING_OFF = 0, LBM_PAIRING_ALL = 1, LBM_PAIRING_EVEN = 2 };
+int lbm_set_pairing(lbm_handle h, int mode);
 
 /* Enable (1, default) or disable (0) CUDA-graph replay in lbm_step. */
 int lbm_set_graphs(lbm_handle h, int enable);

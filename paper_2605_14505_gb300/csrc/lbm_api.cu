@@ -81,7 +81,7 @@ struct lbm_ctx {
     int64_t step = 0;
     int odd = 0;           // layout parity of the store
     int bx = 0, by = 0;
-    bool pairing = true;   // two nodes per thread where a kernel exists (16-bit storage, even nx)
+    int pairing = LBM_PAIRING_EVEN;   // two nodes per thread on even steps (16-bit storage, even nx)
     // diagnostics scratch
     float* diag_fields = nullptr;
     double* diag_partials = nullptr;
@@ -120,14 +120,15 @@ void derive_phys(lbm_ctx* h)
     h->geo.n3 = (uint32_t)((size_t)p.nx * p.ny * p.nz);
 }
 
-bool uses_pairs(const lbm_ctx* h)
+bool uses_pairs(const lbm_ctx* h, int odd)
 {
-    return h->pairing && h->ks->step2[h->p.forcing][0] != nullptr && (h->p.nx % 2) == 0;
+    const bool wanted = h->pairing == LBM_PAIRING_ALL || (h->pairing == LBM_PAIRING_EVEN && !odd);
+    return wanted && h->ks->step2[h->p.forcing][0] != nullptr && (h->p.nx % 2) == 0;
 }
 
 void default_block(lbm_ctx* h)
 {
-    const int xunits = uses_pairs(h) ? h->p.nx / 2 : h->p.nx;
+    const int xunits = uses_pairs(h, 0) ? h->p.nx / 2 : h->p.nx;
     int bx = xunits >= 128 ? 128 : (xunits >= 64 ? 64 : 32);
     int by = 256 / bx;
     while (by > 1 && by / 2 >= h->p.ny) by /= 2;
@@ -195,23 +196,23 @@ int ensure_diag(lbm_ctx* h)
     return LBM_OK;
 }
 
-dim3 step_grid(const lbm_ctx* h)
+dim3 step_grid(const lbm_ctx* h, int odd)
 {
-    const int xunits = uses_pairs(h) ? h->p.nx / 2 : h->p.nx;
+    const int xunits = uses_pairs(h, odd) ? h->p.nx / 2 : h->p.nx;
     return dim3((unsigned)((xunits + h->bx - 1) / h->bx), (unsigned)((h->p.ny + h->by - 1) / h->by),
                 (unsigned)h->p.nz);
 }
 
 cudaError_t launch_step(lbm_ctx* h, int odd, cudaStream_t s)
 {
-    StepArgs a;
+    StepArgs a{};
     a.f = f_ptr(h);
     a.g = g_ptr(h);
     a.geo = h->geo;
     a.ph = h->ph;
     void* args[] = {&a};
-    const void* k = uses_pairs(h) ? h->ks->step2[h->p.forcing][odd] : h->ks->step[h->p.forcing][odd];
-    return cudaLaunchKernel(k, step_grid(h), dim3(h->bx, h->by), args, 0, s);
+    const void* k = uses_pairs(h, odd) ? h->ks->step2[h->p.forcing][odd] : h->ks->step[h->p.forcing][odd];
+    return cudaLaunchKernel(k, step_grid(h, odd), dim3(h->bx, h->by), args, 0, s);
 }
 
 int flat_grid(const lbm_ctx* h)
@@ -799,10 +800,11 @@ int lbm_autotune(lbm_handle h, int reps, double* best_ms_per_step)
     return LBM_OK;
 }
 
-int lbm_set_pairing(lbm_handle h, int enable)
+int lbm_set_pairing(lbm_handle h, int mode)
 {
     if (!h) return fail(LBM_EINVAL, "null handle");
-    h->pairing = enable != 0;
+    if (mode < LBM_PAIRING_OFF || mode > LBM_PAIRING_EVEN) return fail(LBM_EINVAL, "pairing mode must be 0, 1 or 2");
+    h->pairing = mode;
     default_block(h);
     drop_graph(h);
     return LBM_OK;

@@ -307,6 +307,17 @@ LBM_HD float e_dot(float ux, float uy, float uz)
 // !EXACT (16-bit storage, whose rounding of ~5e-4 per step dwarfs the 1e-8
 // effects the exact forms remove): h and k are left as they are and the
 // plain reciprocal is used.
+// Quotient within 2 ulp (__fdividef on the device; the host build, used only
+// to study the arithmetic, divides exactly).
+LBM_HD float fast_div(float a, float b)
+{
+#ifdef __CUDA_ARCH__
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+}
+
 template <class P, bool EXACT = true>
 LBM_HD Macro node_macro(float* h, float* k, const Phys& ph)
 {
@@ -346,7 +357,7 @@ LBM_HD Macro node_macro(float* h, float* k, const Phys& ph)
         m.rho = 1.f + drho;
         m.irho = 1.f / m.rho;
         m.dirho = m.irho - 1.f;
-        m.rho_p = (a + ph.kappa * jz * m.irho) / (1.f + 0.5f * ph.kappa * ph.G * m.irho);
+        m.rho_p = fast_div(a + ph.kappa * jz * m.irho, 1.f + 0.5f * ph.kappa * ph.G * m.irho);
         m.Fz = -ph.G * m.rho_p;
         m.ux = jx * m.irho;
         m.uy = jy * m.irho;
@@ -384,7 +395,7 @@ LBM_HD float bgk(float f, float feq, float dl)
 // f_eq = w (base + rho (e.u)^2 / (2 cs^4)) +- w rho e.u / cs^2, base = drho - rho u^2 / (2 cs^2).
 //
 // f collision (Eqs. 5, 8, 9) with the forcing scheme, in place on h.
-template <class P, int FORCING, bool EXACT = true>
+template <class P, int FORCING>
 LBM_HD void collide_f(float* h, const Macro& m, const Phys& ph)
 {
     using LF = typename P::LF;
@@ -458,41 +469,29 @@ LBM_HD void collide_f(float* h, const Macro& m, const Phys& ph)
             Fs = w * fmaf(m.drho, ps, ps);
             Fa = (ez != 0) ? w * c1 * (float)ez * m.Fz : 0.f;     // w rho e_z du / cs^2
         }
-        if constexpr (EXACT) {
-            // Even and odd parts relax separately: forming hs +- ha first would round
-            // the even part (density, stress) to the ulp of the much larger odd part.
-            const float sp = bgk(h[i], 2.f * hs, dl) + 2.f * Fs;   // h_i + h_j
-            const float dp = bgk(h[j], 2.f * ha, dl) + 2.f * Fa;   // h_i - h_j
-            h[i] = 0.5f * (sp + dp);
-            h[j] = 0.5f * (sp - dp);
-        } else {
-            h[i] = bgk(h[i], hs + ha, dl) + (Fs + Fa);
-            h[j] = bgk(h[j], hs - ha, dl) + (Fs - Fa);
-        }
+        // Even and odd parts relax separately: forming hs +- ha first would round
+        // the even part (density, stress) to the ulp of the much larger odd part.
+        const float sp = bgk(h[i], 2.f * hs, dl) + 2.f * Fs;   // h_i + h_j
+        const float dp = bgk(h[j], 2.f * ha, dl) + 2.f * Fa;   // h_i - h_j
+        h[i] = 0.5f * (sp + dp);
+        h[j] = 0.5f * (sp - dp);
     };
-    if constexpr (EXACT) {
-        sfor<3, kPairs<LF>>([&](auto mc) {
-            constexpr int i = 2 * decltype(mc)::value + 1;
-            const float ha = LF::w(i) * c1 * e_dot<LF, i>(mx, my, mz);
-            if constexpr (LF::ex(i) != 0) ox += (float)LF::ex(i) * ha;
-            if constexpr (LF::ey(i) != 0) oy += (float)LF::ey(i) * ha;
-            if constexpr (LF::ez(i) != 0) oz += (float)LF::ez(i) * ha;
-            relax_pair(mc, ha);
-        });
-        relax_pair(std::integral_constant<int, 0>{}, fmaf(0.5f, mx, -ox));   // slots 1, 2: +-x
-        relax_pair(std::integral_constant<int, 1>{}, fmaf(0.5f, my, -oy));   // slots 3, 4: +-y
-        relax_pair(std::integral_constant<int, 2>{}, fmaf(0.5f, mz, -oz));   // slots 5, 6: +-z
-    } else {
-        sfor<0, kPairs<LF>>([&](auto mc) {
-            constexpr int i = 2 * decltype(mc)::value + 1;
-            relax_pair(mc, LF::w(i) * c1 * e_dot<LF, i>(mx, my, mz));
-        });
-    }
+    sfor<3, kPairs<LF>>([&](auto mc) {
+        constexpr int i = 2 * decltype(mc)::value + 1;
+        const float ha = LF::w(i) * c1 * e_dot<LF, i>(mx, my, mz);
+        if constexpr (LF::ex(i) != 0) ox += (float)LF::ex(i) * ha;
+        if constexpr (LF::ey(i) != 0) oy += (float)LF::ey(i) * ha;
+        if constexpr (LF::ez(i) != 0) oz += (float)LF::ez(i) * ha;
+        relax_pair(mc, ha);
+    });
+    relax_pair(std::integral_constant<int, 0>{}, fmaf(0.5f, mx, -ox));   // slots 1, 2: +-x
+    relax_pair(std::integral_constant<int, 1>{}, fmaf(0.5f, my, -oy));   // slots 3, 4: +-y
+    relax_pair(std::integral_constant<int, 2>{}, fmaf(0.5f, mz, -oz));   // slots 5, 6: +-z
 }
 
 // g collision (Eqs. 11, 12, 14, 15): g_eq = (rho' + rho0) Theta(u), S_i = w_i (-u_z beta).
 // For deviations: g_eq_i - w_i rho0 = w_i (rho' + (rho' + rho0) P_i).
-template <class P, bool EXACT = true>
+template <class P>
 LBM_HD void collide_g(float* k, const Macro& m, const Phys& ph)
 {
     using LG = typename P::LG;
@@ -512,17 +511,132 @@ LBM_HD void collide_g(float* k, const Macro& m, const Phys& ph)
         const float eu = e_dot<LG, i>(m.ux, m.uy, m.uz);
         const float ks = w * fmaf(rr * c2, eu * eu, base);
         const float ka = w * rr * c1 * eu;
-        if constexpr (EXACT) {
-            const float sp = bgk(k[i], 2.f * ks, dl) + 2.f * w * src;
-            const float dp = bgk(k[i + 1], 2.f * ka, dl);
-            k[i] = 0.5f * (sp + dp);
-            k[i + 1] = 0.5f * (sp - dp);
-        } else {
-            const float si = w * src;
-            k[i] = bgk(k[i], ks + ka, dl) + si;
-            k[i + 1] = bgk(k[i + 1], ks - ka, dl) + si;
-        }
+        const float sp = bgk(k[i], 2.f * ks, dl) + 2.f * w * src;
+        const float dp = bgk(k[i + 1], 2.f * ka, dl);
+        k[i] = 0.5f * (sp + dp);
+        k[i + 1] = 0.5f * (sp - dp);
     });
+}
+
+// ---------------------------------------------------------------------------
+// Collisions for 16-bit storage. The same update as collide_f / collide_g
+// written for fewer instructions: BGK as f* = (1 - omega) f + omega f_eq, with
+// omega, the weight and the 1/rho of the equilibrium folded into one
+// coefficient per weight class, and rho (e.u)^2 = (e.j)^2 / rho, so that each
+// opposite pair costs e.j, two multiplies, three FMAs and an add/subtract.
+// FP32 arithmetic still; its rounding is ~1e-7 of values stored to 2^-11
+// (FP16) or 2^-8 (BF16).
+// ---------------------------------------------------------------------------
+template <class P, int FORCING>
+LBM_HD void collide_f_fast(float* h, const Macro& m, const Phys& ph)
+{
+    using LF = typename P::LF;
+    constexpr float c1 = LF::inv_cs2, c2 = LF::half_inv_cs4, c0 = LF::half_inv_cs2;
+    const float om = 2.f - ph.delta_f;   // 1 / tau_f
+    const float cm = ph.delta_f - 1.f;   // 1 - 1 / tau_f
+    // momentum of the equilibrium velocity (as in collide_f)
+    float mx = m.jx, my = m.jy, mz;
+    if constexpr (FORCING == kGuo || FORCING == kHCZ) {
+        mz = m.jz + 0.5f * m.Fz;
+    } else if constexpr (FORCING == kShanChen) {
+        mz = m.jz + ph.sc_tau * m.Fz;
+    } else {
+        mz = m.jz;
+    }
+    const float mv = (mx * mx + my * my + mz * mz) * m.irho;       // rho |v|^2
+    const float base = m.drho - c0 * mv;
+    const float ob = om * base;               // omega (f_eq_i - w_i) / w_i without the e terms
+    const float o2 = om * c2 * m.irho;        // omega rho (e.v)^2 / (2 cs^4) per (e.j)^2
+    const float o1 = om * c1;                 // omega rho e.v / cs^2 per e.j
+    // forcing (Eqs. 8-10 and the cited schemes); v = j_eq / rho
+    const float vz = mz * m.irho;
+    const float gF = ph.guo_pref * m.Fz;
+    const float du = m.Fz * m.irho;
+    const float dusq = du * (2.f * vz + du);
+    {
+        const float heq = LF::w(0) * base + LF::kMassCorr * m.drho + LF::kUsqCorr * mv;
+        float F0 = 0.f;
+        if constexpr (FORCING == kGuo) F0 = -gF * LF::w(0) * c1 * vz;
+        if constexpr (FORCING == kHCZ) {
+            const float vsq = mv * m.irho;
+            F0 = -gF * c1 * vz * LF::w(0) * (1.f - c0 * vsq);
+        }
+        if constexpr (FORCING == kEDM) F0 = (-c0 * LF::w(0) + LF::kUsqCorr) * (m.rho * dusq);
+        h[0] = fmaf(cm, h[0], fmaf(om, heq, F0));
+    }
+    sfor<0, kPairs<LF>>([&](auto mc) {
+        constexpr int i = 2 * decltype(mc)::value + 1;
+        constexpr int j = i + 1;
+        constexpr float w = LF::w(i);
+        constexpr int ez = LF::ez(i);
+        const float em = e_dot<LF, i>(mx, my, mz);
+        float hs = fmaf((w * o2) * em, em, w * ob);
+        float ha = (w * o1) * em;
+        if constexpr (FORCING == kGuo) {
+            const float eu = em * m.irho;
+            hs += gF * w * (ez != 0 ? (2.f * c2 * eu * (float)ez - c1 * vz) : -c1 * vz);
+            ha += gF * w * c1 * (float)ez;
+        } else if constexpr (FORCING == kHCZ) {
+            const float eu = em * m.irho;
+            const float ps = 1.f + c2 * eu * eu - c0 * mv * m.irho;
+            const float pa = c1 * eu;
+            const float c = gF * c1 * w;
+            hs += c * ((float)ez * pa - vz * ps);
+            ha += c * ((float)ez * ps - vz * pa);
+        } else if constexpr (FORCING == kEDM) {
+            float ps = -c0 * dusq;
+            if constexpr (ez != 0) ps += c2 * du * (2.f * (float)ez * (em * m.irho) + du);
+            hs += w * m.rho * ps;
+            if constexpr (ez != 0) ha += w * c1 * (float)ez * m.Fz;
+        }
+        h[i] = fmaf(cm, h[i], hs + ha);
+        h[j] = fmaf(cm, h[j], hs - ha);
+    });
+}
+
+template <class P>
+LBM_HD void collide_g_fast(float* k, const Macro& m, const Phys& ph)
+{
+    using LG = typename P::LG;
+    constexpr float c1 = LG::inv_cs2, c2 = LG::half_inv_cs4, c0 = LG::half_inv_cs2;
+    const float om = 2.f - ph.delta_g;   // 1 / tau_g
+    const float cm = ph.delta_g - 1.f;   // 1 - 1 / tau_g
+    const float usq = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
+    const float rr = m.rho_p + ph.rho0;
+    const float src = ph.c_lbe * (-m.uz * ph.beta);                 // S_i / w_i (Eq. 12)
+    const float base = m.rho_p - c0 * rr * usq;
+    {
+        const float keq = LG::w(0) * base + LG::kMassCorr * m.rho_p + LG::kUsqCorr * rr * usq;
+        k[0] = fmaf(cm, k[0], fmaf(om, keq, (LG::w(0) + LG::kMassCorr) * src));
+    }
+    const float obs = fmaf(om, base, src);
+    const float a2 = om * rr * c2;
+    const float a1 = om * rr * c1;
+    sfor<0, kPairs<LG>>([&](auto mc) {
+        constexpr int i = 2 * decltype(mc)::value + 1;
+        constexpr float w = LG::w(i);
+        const float eu = e_dot<LG, i>(m.ux, m.uy, m.uz);
+        const float ks = fmaf((w * a2) * eu, eu, w * obs);
+        const float ka = (w * a1) * eu;
+        k[i] = fmaf(cm, k[i], ks + ka);
+        k[i + 1] = fmaf(cm, k[i + 1], ks - ka);
+    });
+}
+
+// Moments, coupled solve and both collisions of one node, in place on h, k:
+// the exact FP32 forms for FP32 storage, the short forms for 16-bit storage.
+template <class P, int FORCING, bool EXACT>
+LBM_HD Macro collide_node(float* h, float* k, const Phys& ph)
+{
+    const Macro m = node_macro<P, EXACT>(h, k, ph);
+    if constexpr (EXACT) {
+        collide_f<P, FORCING>(h, m, ph);
+        collide_g<P>(k, m, ph);
+    } else {
+        collide_f_fast<P, FORCING>(h, m, ph);
+        collide_g_fast<P>(k, m, ph);
+    }
+    return m;
 }
 
 }  // namespace lbm

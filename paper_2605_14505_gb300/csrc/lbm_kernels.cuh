@@ -27,9 +27,7 @@ __device__ __forceinline__ void update_node(void* fv, void* gv, const Geometry& 
     float h[P::QF], k[P::QG];
     load_node<typename P::LF, ODD, T>(f, n3, a, h);
     load_node<typename P::LG, ODD, T>(g, n3, a, k);
-    const Macro m = node_macro<P, kExact>(h, k, ph);
-    collide_f<P, FORCING, kExact>(h, m, ph);
-    collide_g<P, kExact>(k, m, ph);
+    collide_node<P, FORCING, kExact>(h, k, ph);
     const NodeAddr b(geo, (int)launder(x), (int)launder(y), (int)launder(z));
     store_node<typename P::LF, ODD, T>(f, n3, b, h);
     store_node<typename P::LG, ODD, T>(g, n3, b, k);
@@ -172,9 +170,7 @@ __global__ void __launch_bounds__(256, 2) k_step2(StepArgs args)
         for (int i = 0; i < P::QF; ++i) h[i] = Pack16<T>::lo(wf[i]);
 #pragma unroll
         for (int i = 0; i < P::QG; ++i) k[i] = Pack16<T>::lo(wg[i]);
-        const Macro m = node_macro<P, false>(h, k, args.ph);
-        collide_f<P, FORCING, false>(h, m, args.ph);
-        collide_g<P, false>(k, m, args.ph);
+        collide_node<P, FORCING, false>(h, k, args.ph);
 #pragma unroll
         for (int i = 0; i < P::QF; ++i) wf[i] = __byte_perm(wf[i], Pack16<T>::bits(h[i]), 0x3254);
 #pragma unroll
@@ -186,9 +182,7 @@ __global__ void __launch_bounds__(256, 2) k_step2(StepArgs args)
         for (int i = 0; i < P::QF; ++i) h[i] = Pack16<T>::hi(wf[i]);
 #pragma unroll
         for (int i = 0; i < P::QG; ++i) k[i] = Pack16<T>::hi(wg[i]);
-        const Macro m = node_macro<P, false>(h, k, args.ph);
-        collide_f<P, FORCING, false>(h, m, args.ph);
-        collide_g<P, false>(k, m, args.ph);
+        collide_node<P, FORCING, false>(h, k, args.ph);
 #pragma unroll
         for (int i = 0; i < P::QF; ++i) wf[i] = __byte_perm(wf[i], Pack16<T>::bits(h[i]), 0x5410);
 #pragma unroll

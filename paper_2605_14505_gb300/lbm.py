@@ -316,8 +316,14 @@ def lbm_autotune(h, reps: int = 3) -> float:
     return ms.value
 
 
-def lbm_set_pairing(h, enable: bool):
-    _check(load_library().lbm_set_pairing(h, 1 if enable else 0))
+PAIRING = {"off": 0, "all": 1, "even": 2}
+
+
+def lbm_set_pairing(h, mode):
+    """mode: "off", "all", "even" (or 0/1/2; True/False mean "all"/"off")."""
+    if isinstance(mode, str):
+        mode = PAIRING[mode]
+    _check(load_library().lbm_set_pairing(h, int(mode)))
 
 
 def lbm_set_graphs(h, enable: bool):

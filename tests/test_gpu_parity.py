@@ -251,12 +251,14 @@ def test_checkpoint_roundtrip():
     assert np.max(np.abs(fa - fb)) == 0.0 and np.max(np.abs(ga - gb)) == 0.0
 
 
+@pytest.mark.parametrize("mode", ["all", "even"])
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
 @pytest.mark.parametrize("shape", [(2, 3, 2), (34, 6, 4), (64, 5, 3), (258, 2, 2)])
-def test_pair_kernel_matches_single_node_kernel(storage, shape):
-    """16-bit storage with even nx runs two nodes per thread; the per-node
-    arithmetic is the one-node kernel's, so both agree to the storage
-    rounding (nx = 2 makes x0 - 1 and x0 + 2 wrap onto the pair itself)."""
+def test_pair_kernel_matches_single_node_kernel(mode, storage, shape):
+    """16-bit storage with even nx runs two nodes per thread (on every step,
+    or on even steps only); the per-node arithmetic is the one-node kernel's,
+    so both agree to the storage rounding (nx = 2 makes x0 - 1 and x0 + 2
+    wrap onto the pair itself)."""
     N = 3e-3
     p = lattice_params(*shape, "27x19", "sc", 0.55, 0.6, N * LAM, -N / LAM)
     n3 = shape[0] * shape[1] * shape[2]
@@ -264,7 +266,10 @@ def test_pair_kernel_matches_single_node_kernel(storage, shape):
     xf, xg = I.neq_noise(n3, 10), I.neq_noise(n3, 11)
     a = gpu_sim(p, storage)
     b = gpu_sim(p, storage)
-    lbm.lbm_set_pairing(b.h, False)
+    lbm.lbm_set_pairing(a.h, mode)
+    lbm.lbm_set_pairing(b.h, "off")
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_set_pairing(b.h, 3)
     for s in (a, b):
         s.init_fields(rho, u, rp, xf, xg, 1e-3)
     for _ in range(3):  # odd, even, odd layouts
