@@ -424,7 +424,7 @@ def main():
                     help="run a small profiling case instead of the benchmark")
     ap.add_argument("--ncu-n", type=int, default=128)
     ap.add_argument("--ncu-steps", type=int, default=6)
-    ap.add_argument("--ncu-pairing", choices=["off", "all", "even"], default="even",
+    ap.add_argument("--ncu-pairing", choices=["off", "all", "even"], default="all",
                     help="profiling case: nodes per thread for 16-bit storage (lbm_set_pairing)")
     args = ap.parse_args()
     if args.ncu_case:

@@ -244,11 +244,12 @@ int lbm_autotune(lbm_handle h, int reps, double* best_ms_per_step);
 
 /* For FP16/BF16 storage and even nx the step kernel can update two
  * x-adjacent nodes per thread, moving each pair's values of a slot as one
- * 32-bit word where the AA access keeps them aligned; the per-node arithmetic
- * is the same, so the results are bitwise those of the one-node kernel.
- * mode: LBM_PAIRING_OFF (one node per thread), LBM_PAIRING_ALL (two nodes per
- * thread at both AA parities), LBM_PAIRING_EVEN (the default: two nodes on
- * even steps, whose accesses are all aligned, one node on odd steps).
+ * 32-bit word where the AA access keeps them aligned (every slot of the even
+ * step; on the odd step, whose pairs are (x0 - 1, x0), the slots with
+ * e_x != 0); the per-node arithmetic is the one-node kernel's.
+ * mode: LBM_PAIRING_OFF (one node per thread), LBM_PAIRING_ALL (the default:
+ * two nodes per thread at both AA parities), LBM_PAIRING_EVEN (two nodes on
+ * even steps, one node on odd steps).
  * Ignored for FP32 storage and odd nx. Resets the launch shape to its
  * default. Error: LBM_EINVAL for another mode. */
 enum lbm_pairing { LBM_PAIRING_OFF = 0, LBM_PAIRING_ALL = 1, LBM_PAIRING_EVEN = 2 };

@@ -81,7 +81,7 @@ struct lbm_ctx {
     int64_t step = 0;
     int odd = 0;           // layout parity of the store
     int bx = 0, by = 0;
-    int pairing = LBM_PAIRING_EVEN;   // two nodes per thread on even steps (16-bit storage, even nx)
+    int pairing = LBM_PAIRING_ALL;   // two nodes per thread (16-bit storage, even nx)
     // diagnostics scratch
     float* diag_fields = nullptr;
     double* diag_partials = nullptr;

@@ -51,12 +51,14 @@ __global__ void __launch_bounds__(256, LBM_STEP_MINBLOCKS) k_step(StepArgs args)
 }
 
 // ---------------------------------------------------------------------------
-// 16-bit storage, two x-adjacent nodes (x0 even, x0 + 1) per thread, nx even.
-// The pair's values of one slot are one aligned 32-bit word wherever the AA
-// access keeps them adjacent and aligned (every slot of the even step; the
-// e_x = 0 slots of the odd step), else two 16-bit accesses. Loads, stores and
-// address arithmetic are shared by the two nodes, and the two results of a
-// slot are packed by one conversion instruction.
+// 16-bit storage, two x-adjacent nodes per thread, nx even. Thread t takes
+// x0 = 2 t and the nodes (x0, x0 + 1) on even steps, (x0 - 1, x0) on odd
+// steps (x0 - 1 wrapped), low half first. The pair's values of one slot are
+// then one aligned 32-bit word for every slot of the even step and for the
+// e_x != 0 slots of the odd step, whose AA accesses at x -+ e_x land on
+// (x0 - 2, x0 - 1) or (x0, x0 + 1); the odd step's e_x = 0 slots are two
+// 16-bit accesses. Loads, stores and address arithmetic are shared by the two
+// nodes, and the two results of a slot are packed by one conversion.
 // ---------------------------------------------------------------------------
 template <class T>
 struct Pack16;
@@ -83,22 +85,32 @@ struct Pack16<__nv_bfloat16> {
     static __device__ __forceinline__ uint32_t bits(float a) { return __bfloat16_as_ushort(__float2bfloat16_rn(a)); }
 };
 
-// Element offsets around the pair: X[p] for x0 - 1, x0, x0 + 1, x0 + 2 (wrapped).
+// Element offsets around the pair: X[0] = x0 - 2, X[1] = x0 - 1 (both
+// wrapped), X[2] = x0; Y and Z for y -1, 0, +1 and z -1, 0, +1.
 struct PairAddr {
-    uint32_t X[4], Y[3], Z[3];
+    uint32_t X[3], Y[3], Z[3];
     __device__ __forceinline__ PairAddr(const Geometry& g, int x0, int y, int z)
     {
-        const int xm = (x0 == 0) ? g.nx - 1 : x0 - 1;
-        const int x2 = (x0 + 2 == g.nx) ? 0 : x0 + 2;
+        const int xm2 = (x0 == 0) ? g.nx - 2 : x0 - 2;
+        const int xm1 = (x0 == 0) ? g.nx - 1 : x0 - 1;
         const int ym = (y == 0) ? g.ny - 1 : y - 1, yp = (y == g.ny - 1) ? 0 : y + 1;
         const int zm = (z == 0) ? g.nz - 1 : z - 1, zp = (z == g.nz - 1) ? 0 : z + 1;
         const uint32_t nxy = (uint32_t)g.nx * (uint32_t)g.ny;
-        X[0] = xm; X[1] = x0; X[2] = x0 + 1; X[3] = x2;
+        X[0] = xm2; X[1] = xm1; X[2] = x0;
         Y[0] = ym * g.nx; Y[1] = y * g.nx; Y[2] = yp * g.nx;
         Z[0] = zm * nxy; Z[1] = z * nxy; Z[2] = zp * nxy;
     }
     __device__ __forceinline__ uint32_t off(int p, int sy, int sz) const { return Z[sz + 1] + Y[sy + 1] + X[p]; }
 };
+
+__device__ __forceinline__ uint32_t ld_word(const unsigned short* p)
+{
+    return __ldcs(reinterpret_cast<const unsigned int*>(p));
+}
+__device__ __forceinline__ void st_word(unsigned short* p, uint32_t w)
+{
+    __stcs(reinterpret_cast<unsigned int*>(p), w);
+}
 
 template <class L, bool ODD>
 __device__ __forceinline__ void load_pair(const unsigned short* __restrict__ b16, uint32_t n3, const PairAddr& a,
@@ -108,15 +120,17 @@ __device__ __forceinline__ void load_pair(const unsigned short* __restrict__ b16
         constexpr int i = decltype(ic)::value;
         constexpr int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
         if constexpr (!ODD) {
-            w[i] = __ldcs(reinterpret_cast<const unsigned int*>(b16 + ((uint32_t)i * n3 + a.off(1, 0, 0))));
+            w[i] = ld_word(b16 + ((uint32_t)i * n3 + a.off(2, 0, 0)));
         } else {
+            // nodes x0 - 1 and x0 read slot opp(i) at x - e_i
             const uint32_t s = (uint32_t)L::opp(i) * n3;
-            if constexpr (ex == 0) {
-                w[i] = __ldcs(reinterpret_cast<const unsigned int*>(b16 + (s + a.off(1, -ey, -ez))));
+            if constexpr (ex == 1) {
+                w[i] = ld_word(b16 + (s + a.off(0, -ey, -ez)));   // (x0 - 2, x0 - 1)
+            } else if constexpr (ex == -1) {
+                w[i] = ld_word(b16 + (s + a.off(2, -ey, -ez)));   // (x0, x0 + 1)
             } else {
-                constexpr int pa = (ex == 1) ? 0 : 2;   // sources x0 - e_x and x0 + 1 - e_x
-                const uint32_t lo = __ldcs(b16 + (s + a.off(pa, -ey, -ez)));
-                const uint32_t hi = __ldcs(b16 + (s + a.off(pa + 1, -ey, -ez)));
+                const uint32_t lo = __ldcs(b16 + (s + a.off(1, -ey, -ez)));
+                const uint32_t hi = __ldcs(b16 + (s + a.off(2, -ey, -ez)));
                 w[i] = lo | (hi << 16);
             }
         }
@@ -131,15 +145,17 @@ __device__ __forceinline__ void store_pair(unsigned short* __restrict__ b16, uin
         constexpr int i = decltype(ic)::value;
         constexpr int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
         if constexpr (!ODD) {
-            __stcs(reinterpret_cast<unsigned int*>(b16 + ((uint32_t)L::opp(i) * n3 + a.off(1, 0, 0))), w[i]);
+            st_word(b16 + ((uint32_t)L::opp(i) * n3 + a.off(2, 0, 0)), w[i]);
         } else {
+            // nodes x0 - 1 and x0 write slot i at x + e_i
             const uint32_t s = (uint32_t)i * n3;
-            if constexpr (ex == 0) {
-                __stcs(reinterpret_cast<unsigned int*>(b16 + (s + a.off(1, ey, ez))), w[i]);
+            if constexpr (ex == 1) {
+                st_word(b16 + (s + a.off(2, ey, ez)), w[i]);      // (x0, x0 + 1)
+            } else if constexpr (ex == -1) {
+                st_word(b16 + (s + a.off(0, ey, ez)), w[i]);      // (x0 - 2, x0 - 1)
             } else {
-                constexpr int pa = (ex == 1) ? 2 : 0;   // destinations x0 + e_x and x0 + 1 + e_x
-                __stcs(b16 + (s + a.off(pa, ey, ez)), (unsigned short)(w[i] & 0xffffu));
-                __stcs(b16 + (s + a.off(pa + 1, ey, ez)), (unsigned short)(w[i] >> 16));
+                __stcs(b16 + (s + a.off(1, ey, ez)), (unsigned short)(w[i] & 0xffffu));
+                __stcs(b16 + (s + a.off(2, ey, ez)), (unsigned short)(w[i] >> 16));
             }
         }
     });
@@ -161,9 +177,9 @@ __global__ void __launch_bounds__(256, 2) k_step2(StepArgs args)
         load_pair<typename P::LF, ODD>(fb, n3, a, wf);
         load_pair<typename P::LG, ODD>(gb, n3, a, wg);
     }
-    // Node x0 (low halves), then node x0 + 1 (high halves): each result goes
-    // back into its half of the word before the other node is unpacked, so
-    // only one node's 46 values are live in FP32 at a time.
+    // The low-half node, then the high-half node: each result goes back into
+    // its half of the word before the other node is unpacked, so only one
+    // node's values are live in FP32 at a time.
     {
         float h[P::QF], k[P::QG];
 #pragma unroll
