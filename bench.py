@@ -39,6 +39,32 @@ METRIC = "DDF MLUPS (FP32 storage) & % of HBM roofline; FP16-storage vs FP32 at 
 WORKLOAD = "stratified TGV 256^3, D3Q27xD3Q19, velocity-shift (Shan-Chen) forcing, Re 800, Fr 0.1, Pr 1, U0 0.04"
 
 
+# DRAM bytes per step-kernel launch on the 256^3 bench lattice
+# (dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture, mean of
+# an even and an odd launch), with the fingerprint of the kernel sources the
+# capture ran; reported as null once the sources differ from it.
+NCU_TRAFFIC = {"fingerprint": "53f6d0d4618fffb2", "fp32": 6117114496, "fp16": 3025986048, "bf16": 3025766400}
+
+
+def source_fingerprint() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2605_14505_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(storage: str):
+    if NCU_TRAFFIC["fingerprint"] != source_fingerprint():
+        return None
+    return NCU_TRAFFIC.get(storage)
+
+
 def bytes_per_node(storage: str) -> int:
     # every population read once and written once per update
     return (27 + 19) * 2 * (4 if storage == "fp32" else 2)
@@ -216,7 +242,8 @@ def run_gpu_arm(args):
             "mlups": round(vmlups, 1), "speedup_vs_fp32": round(vmlups / value, 3),
             "step_kernel_ms": round(vstep_ms, 4),
             "roofline": {"bound": "hbm", "achieved": round(vach, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(vach / peak, 4)},
+                         "frac": round(vach / peak, 4), "traffic": ncu_traffic(storage),
+                         "algorithmic_bytes_per_launch": bytes_per_node(storage) * n3},
             "rel_dev_vs_fp32_gpu": {k: float(f"{v:.3e}") for k, v in err.items()},
             "bytes_per_node": bytes_per_node(storage),
         }
@@ -266,7 +293,8 @@ def run_gpu_arm(args):
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (3.09 GB store vs 129 MB L2)", "block": [bx, by]},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "frac": round(achieved / peak, 4), "traffic": ncu_traffic("fp32"),
+                     "algorithmic_bytes_per_launch": bytes_per_node("fp32") * n3,
                      "kernel": "k_step<27x19, SC, f32> (even/odd AA)", "peak_kind": peak_kind,
                      "bytes_per_node": bytes_per_node("fp32"), "step_kernel_ms": round(step_ms, 4),
                      "diag_ms": round(diag_ms, 4)},
@@ -397,8 +425,8 @@ def run_ncu_case(args):
     from paper_2605_14505_gb300 import lbm
 
     storage, pair = args.ncu_case, PAIR
-    if args.ncu_case == "19x7":
-        storage, pair = "fp32", "19x7"
+    if args.ncu_case.startswith("19x7"):
+        storage, pair = ("fp16" if args.ncu_case.endswith("fp16") else "fp32"), "19x7"
     p = lbm.lbm_params_from_physics(args.ncu_n, args.ncu_n, args.ncu_n, pair, FORCING, RE, FR, PR, U0)
     sim = lbm.Simulation(p, storage=storage)
     lbm.lbm_set_graphs(sim.h, False)
@@ -408,7 +436,8 @@ def run_ncu_case(args):
     d = sim.diagnostics()
     sim.close()
     torch.cuda.synchronize()
-    print(json.dumps({"ncu_case": args.ncu_case, "n": args.ncu_n, "steps": args.ncu_steps, "Ek": d["Ek"]}))
+    print(json.dumps({"ncu_case": args.ncu_case, "n": args.ncu_n, "steps": args.ncu_steps, "Ek": d["Ek"],
+                      "sources": source_fingerprint()}))
 
 
 def main():
@@ -420,7 +449,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched sweep")
-    ap.add_argument("--ncu-case", choices=["fp32", "fp16", "bf16", "19x7"], default=None,
+    ap.add_argument("--ncu-case", choices=["fp32", "fp16", "bf16", "19x7", "19x7-fp16"], default=None,
                     help="run a small profiling case instead of the benchmark")
     ap.add_argument("--ncu-n", type=int, default=128)
     ap.add_argument("--ncu-steps", type=int, default=6)

@@ -161,8 +161,14 @@ __device__ __forceinline__ void store_pair(unsigned short* __restrict__ b16, uin
     });
 }
 
+// Two 256-thread blocks per SM (<= 128 registers) for D3Q27xD3Q19, whose 46
+// packed words and one node's 46 FP32 values are live together; three
+// (<= 85 registers) for the smaller pairs.
+template <class P>
+constexpr int kStep2MinBlocks = (P::QF + P::QG <= 34) ? 3 : 2;
+
 template <class P, int FORCING, class T, bool ODD>
-__global__ void __launch_bounds__(256, 2) k_step2(StepArgs args)
+__global__ void __launch_bounds__(256, kStep2MinBlocks<P>) k_step2(StepArgs args)
 {
     const int x0 = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
