@@ -431,6 +431,7 @@ def run_ncu_case(args):
     sim = lbm.Simulation(p, storage=storage)
     lbm.lbm_set_graphs(sim.h, False)
     lbm.lbm_set_pairing(sim.h, args.ncu_pairing)
+    lbm.lbm_set_tile_staging(sim.h, args.ncu_staging)
     sim.init_tgv(seed=1, noise_amp=1e-3)
     sim.step(args.ncu_steps)
     d = sim.diagnostics()
@@ -455,6 +456,8 @@ def main():
     ap.add_argument("--ncu-steps", type=int, default=6)
     ap.add_argument("--ncu-pairing", choices=["off", "all", "even"], default="all",
                     help="profiling case: nodes per thread for 16-bit storage (lbm_set_pairing)")
+    ap.add_argument("--ncu-staging", action="store_true",
+                    help="profiling case: bulk-copy tile staging for 16-bit storage (lbm_set_tile_staging)")
     args = ap.parse_args()
     if args.ncu_case:
         run_ncu_case(args)

@@ -255,6 +255,29 @@ int lbm_autotune(lbm_handle h, int reps, double* best_ms_per_step);
 enum lbm_pairing { LBM_PAIRING_OFF = 0, LBM_PAIRING_ALL = 1, LBM_PAIRING_EVEN = 2 };
 int lbm_set_pairing(lbm_handle h, int mode);
 
+/* Tile staging (FP16/BF16 storage, nx a multiple of 64; off by default):
+ * the step kernel is persistent; for each tile of W nodes of an
+ * x-row (W = 256, 128 or 64, the largest dividing nx) warp 0 issues one bulk
+ * asynchronous copy (cp.async.bulk, completion on an mbarrier) per slot row
+ * into shared memory, one tile ahead of the compute, and two nodes per thread
+ * update from there; the per-node arithmetic and the stores are those of the
+ * two-nodes-per-thread kernel (Eqs. 5-18 as in lbm_step). enable = 0 returns
+ * to the kernels selected by lbm_set_pairing. Every wait on a copy is
+ * bounded; a wait that runs out makes the next lbm_synchronize return
+ * LBM_ETIMEOUT (the lattice state is then not valid). */
+int lbm_set_tile_staging(lbm_handle h, int enable);
+
+/* *width = the tile width the staged kernel uses for this lattice, or 0 if
+ * the step runs without tile staging (FP32 storage, nx not a multiple of 64,
+ * staging disabled, or no store yet). */
+int lbm_uses_tile_staging(lbm_handle h, int* width);
+
+/* Test hook for the bounded waits of tile staging: every tile expects
+ * extra_tx_bytes more than its copies deliver (so with extra_tx_bytes > 0 no
+ * wait can complete) and each wait polls at most spin_limit times. (0, 1 << 22)
+ * restores normal operation. Error: LBM_EINVAL for spin_limit = 0. */
+int lbm_set_stage_test(lbm_handle h, unsigned extra_tx_bytes, unsigned spin_limit);
+
 /* Enable (1, default) or disable (0) CUDA-graph replay in lbm_step. */
 int lbm_set_graphs(lbm_handle h, int enable);
 

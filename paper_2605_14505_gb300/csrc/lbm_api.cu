@@ -15,6 +15,7 @@
 #include "../../include/lbm.h"
 #include "lbm_dispatch.h"
 #include "lbm_kernels.cuh"
+#include "lbm_stage.cuh"
 
 using namespace lbm;
 
@@ -82,6 +83,11 @@ struct lbm_ctx {
     int odd = 0;           // layout parity of the store
     int bx = 0, by = 0;
     int pairing = LBM_PAIRING_ALL;   // two nodes per thread (16-bit storage, even nx)
+    bool tile_staging = false;        // bulk-copy staged kernel where it applies
+    int stage_grid = 0;               // persistent grid of the staged kernel (0: not derived yet)
+    int* d_err = nullptr;             // device flag raised by a bounded wait that ran out
+    uint32_t stage_spin = 1u << 22;   // mbarrier polls per wait
+    uint32_t stage_extra_tx = 0;      // test hook: bytes expected beyond the copies
     // diagnostics scratch
     float* diag_fields = nullptr;
     double* diag_partials = nullptr;
@@ -118,6 +124,17 @@ void derive_phys(lbm_ctx* h)
     h->geo.ny = p.ny;
     h->geo.nz = p.nz;
     h->geo.n3 = (uint32_t)((size_t)p.nx * p.ny * p.nz);
+}
+
+// Tile width of the staged kernel (a multiple of 64 that divides nx), or 0
+// where it does not apply: FP32 storage, nx not a multiple of 64, or a store
+// not 16-byte aligned (bulk copies need 16-byte aligned rows).
+int stage_width(const lbm_ctx* h)
+{
+    if (!h->tile_staging || h->ks->staged[h->p.forcing][0] == nullptr || h->store == nullptr) return 0;
+    if (reinterpret_cast<uintptr_t>(h->store) % 16 != 0) return 0;
+    const int nx = h->p.nx;
+    return nx % 256 == 0 ? 256 : nx % 128 == 0 ? 128 : nx % 64 == 0 ? 64 : 0;
 }
 
 bool uses_pairs(const lbm_ctx* h, int odd)
@@ -203,8 +220,40 @@ dim3 step_grid(const lbm_ctx* h, int odd)
                 (unsigned)h->p.nz);
 }
 
+cudaError_t launch_staged(lbm_ctx* h, int odd, int W, cudaStream_t s)
+{
+    const void* k = h->ks->staged[h->p.forcing][odd];
+    const size_t smem = stage_smem_bytes(h->q.qf + h->q.qg, W);
+    StageArgs a{};
+    a.f = f_ptr(h);
+    a.g = g_ptr(h);
+    a.geo = h->geo;
+    a.ph = h->ph;
+    a.W = W;
+    a.ntx = h->p.nx / W;
+    a.ntiles = (uint32_t)a.ntx * (uint32_t)h->p.ny * (uint32_t)h->p.nz;
+    a.err = h->d_err;
+    a.spin_limit = h->stage_spin;
+    a.extra_tx = h->stage_extra_tx;
+    if (h->stage_grid == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(h->ks->staged[h->p.forcing][odd ^ 1],
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int occ = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, W / 2, smem);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) return cudaErrorInvalidConfiguration;
+        const size_t cap = (size_t)(h->num_sms > 0 ? h->num_sms : 1) * (size_t)occ;
+        h->stage_grid = (int)(a.ntiles < cap ? a.ntiles : cap);
+    }
+    void* args[] = {&a};
+    return cudaLaunchKernel(k, dim3((unsigned)h->stage_grid), dim3((unsigned)(W / 2)), args, smem, s);
+}
+
 cudaError_t launch_step(lbm_ctx* h, int odd, cudaStream_t s)
 {
+    const int W = stage_width(h);
+    if (W > 0) return launch_staged(h, odd, W, s);
     StepArgs a{};
     a.f = f_ptr(h);
     a.g = g_ptr(h);
@@ -352,6 +401,13 @@ int lbm_create_params(lbm_handle* out, const lbm_params* p)
         return cuda_fail(e, "cudaStreamCreate");
     }
     h->own_stream = true;
+    if (cudaMalloc(&h->d_err, sizeof(int)) != cudaSuccess || cudaMemset(h->d_err, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        if (h->d_err) cudaFree(h->d_err);
+        cudaStreamDestroy(h->stream);
+        delete h;
+        return fail(LBM_ENOMEM, "device error-flag allocation failed");
+    }
     *out = h;
     return LBM_OK;
 }
@@ -381,6 +437,7 @@ int lbm_set_storage(lbm_handle h, int storage)
     if (!ks) return fail(LBM_EUNSUPPORTED, "storage %d is not compiled in for pair %d", storage, h->p.pair);
     h->p.storage = storage;
     h->ks = ks;
+    h->stage_grid = 0;
     default_block(h);
     drop_graph(h);
     return LBM_OK;
@@ -537,6 +594,13 @@ int lbm_synchronize(lbm_handle h)
     int rc = check_handle(h);
     if (rc) return rc;
     LBM_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    int err = 0;
+    LBM_CUDA(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag read");
+    if (err) {
+        LBM_CUDA(cudaMemset(h->d_err, 0, sizeof(int)), "error flag reset");
+        return fail(LBM_ETIMEOUT, "a shared-memory staging wait of the step kernel ran out; the lattice state "
+                                  "is not valid");
+    }
     return LBM_OK;
 }
 
@@ -810,6 +874,32 @@ int lbm_set_pairing(lbm_handle h, int mode)
     return LBM_OK;
 }
 
+int lbm_set_tile_staging(lbm_handle h, int enable)
+{
+    if (!h) return fail(LBM_EINVAL, "null handle");
+    h->tile_staging = enable != 0;
+    h->stage_grid = 0;
+    drop_graph(h);
+    return LBM_OK;
+}
+
+int lbm_uses_tile_staging(lbm_handle h, int* width)
+{
+    if (!h || !width) return fail(LBM_EINVAL, "null argument");
+    *width = stage_width(h);
+    return LBM_OK;
+}
+
+int lbm_set_stage_test(lbm_handle h, unsigned extra_tx_bytes, unsigned spin_limit)
+{
+    if (!h) return fail(LBM_EINVAL, "null handle");
+    if (spin_limit == 0) return fail(LBM_EINVAL, "spin_limit must be positive");
+    h->stage_extra_tx = extra_tx_bytes;
+    h->stage_spin = spin_limit;
+    drop_graph(h);
+    return LBM_OK;
+}
+
 int lbm_set_graphs(lbm_handle h, int enable)
 {
     if (!h) return fail(LBM_EINVAL, "null handle");
@@ -930,6 +1020,7 @@ int lbm_destroy(lbm_handle h)
     if (h->diag_partials) cudaFree(h->diag_partials);
     if (h->diag_out) cudaFree(h->diag_out);
     if (h->diag_host) cudaFreeHost(h->diag_host);
+    if (h->d_err) cudaFree(h->d_err);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return LBM_OK;

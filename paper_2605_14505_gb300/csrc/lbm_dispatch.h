@@ -9,6 +9,7 @@ struct KernelSet {
     int qf, qg;
     const void* step[4][2];   // [forcing][odd]
     const void* step2[4][2];  // two nodes per thread (16-bit storage, even nx), or null
+    const void* staged[4][2]; // two nodes per thread, bulk-copy staged tiles (16-bit storage), or null
     const void* init_fields;
     const void* init_tgv;
     const void* get_pops;

@@ -161,6 +161,38 @@ __device__ __forceinline__ void store_pair(unsigned short* __restrict__ b16, uin
     });
 }
 
+// Both nodes of a pair, in place on the packed words: the low-half node, then
+// the high-half node. Each result goes back into its half of the word before
+// the other node is unpacked, so only one node's values are live in FP32.
+template <class P, int FORCING, class T>
+__device__ __forceinline__ void collide_pair_words(uint32_t* wf, uint32_t* wg, const Phys& ph)
+{
+    {
+        float h[P::QF], k[P::QG];
+#pragma unroll
+        for (int i = 0; i < P::QF; ++i) h[i] = Pack16<T>::lo(wf[i]);
+#pragma unroll
+        for (int i = 0; i < P::QG; ++i) k[i] = Pack16<T>::lo(wg[i]);
+        collide_node<P, FORCING, false>(h, k, ph);
+#pragma unroll
+        for (int i = 0; i < P::QF; ++i) wf[i] = __byte_perm(wf[i], Pack16<T>::bits(h[i]), 0x3254);
+#pragma unroll
+        for (int i = 0; i < P::QG; ++i) wg[i] = __byte_perm(wg[i], Pack16<T>::bits(k[i]), 0x3254);
+    }
+    {
+        float h[P::QF], k[P::QG];
+#pragma unroll
+        for (int i = 0; i < P::QF; ++i) h[i] = Pack16<T>::hi(wf[i]);
+#pragma unroll
+        for (int i = 0; i < P::QG; ++i) k[i] = Pack16<T>::hi(wg[i]);
+        collide_node<P, FORCING, false>(h, k, ph);
+#pragma unroll
+        for (int i = 0; i < P::QF; ++i) wf[i] = __byte_perm(wf[i], Pack16<T>::bits(h[i]), 0x5410);
+#pragma unroll
+        for (int i = 0; i < P::QG; ++i) wg[i] = __byte_perm(wg[i], Pack16<T>::bits(k[i]), 0x5410);
+    }
+}
+
 // Two 256-thread blocks per SM (<= 128 registers) for D3Q27xD3Q19, whose 46
 // packed words and one node's 46 FP32 values are live together; three
 // (<= 85 registers) for the smaller pairs.
@@ -183,33 +215,7 @@ __global__ void __launch_bounds__(256, kStep2MinBlocks<P>) k_step2(StepArgs args
         load_pair<typename P::LF, ODD>(fb, n3, a, wf);
         load_pair<typename P::LG, ODD>(gb, n3, a, wg);
     }
-    // The low-half node, then the high-half node: each result goes back into
-    // its half of the word before the other node is unpacked, so only one
-    // node's values are live in FP32 at a time.
-    {
-        float h[P::QF], k[P::QG];
-#pragma unroll
-        for (int i = 0; i < P::QF; ++i) h[i] = Pack16<T>::lo(wf[i]);
-#pragma unroll
-        for (int i = 0; i < P::QG; ++i) k[i] = Pack16<T>::lo(wg[i]);
-        collide_node<P, FORCING, false>(h, k, args.ph);
-#pragma unroll
-        for (int i = 0; i < P::QF; ++i) wf[i] = __byte_perm(wf[i], Pack16<T>::bits(h[i]), 0x3254);
-#pragma unroll
-        for (int i = 0; i < P::QG; ++i) wg[i] = __byte_perm(wg[i], Pack16<T>::bits(k[i]), 0x3254);
-    }
-    {
-        float h[P::QF], k[P::QG];
-#pragma unroll
-        for (int i = 0; i < P::QF; ++i) h[i] = Pack16<T>::hi(wf[i]);
-#pragma unroll
-        for (int i = 0; i < P::QG; ++i) k[i] = Pack16<T>::hi(wg[i]);
-        collide_node<P, FORCING, false>(h, k, args.ph);
-#pragma unroll
-        for (int i = 0; i < P::QF; ++i) wf[i] = __byte_perm(wf[i], Pack16<T>::bits(h[i]), 0x5410);
-#pragma unroll
-        for (int i = 0; i < P::QG; ++i) wg[i] = __byte_perm(wg[i], Pack16<T>::bits(k[i]), 0x5410);
-    }
+    collide_pair_words<P, FORCING, T>(wf, wg, args.ph);
     const PairAddr b(args.geo, (int)launder(x0), (int)launder(y), (int)launder(z));
     store_pair<typename P::LF, ODD>(fb, n3, b, wf);
     store_pair<typename P::LG, ODD>(gb, n3, b, wg);

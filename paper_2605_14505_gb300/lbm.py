@@ -104,6 +104,9 @@ _SIGS = {
     "lbm_autotune": ([_H, ctypes.c_int, _DP], ctypes.c_int),
     "lbm_set_graphs": ([_H, ctypes.c_int], ctypes.c_int),
     "lbm_set_pairing": ([_H, ctypes.c_int], ctypes.c_int),
+    "lbm_set_tile_staging": ([_H, ctypes.c_int], ctypes.c_int),
+    "lbm_uses_tile_staging": ([_H, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "lbm_set_stage_test": ([_H, ctypes.c_uint, ctypes.c_uint], ctypes.c_int),
     "lbm_destroy": ([_H], ctypes.c_int),
     "lbm_batch_create": ([ctypes.POINTER(_H), ctypes.POINTER(lbm_params), ctypes.c_int], ctypes.c_int),
     "lbm_batch_count": ([_H, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -324,6 +327,20 @@ def lbm_set_pairing(h, mode):
     if isinstance(mode, str):
         mode = PAIRING[mode]
     _check(load_library().lbm_set_pairing(h, int(mode)))
+
+
+def lbm_set_tile_staging(h, enable: bool):
+    _check(load_library().lbm_set_tile_staging(h, 1 if enable else 0))
+
+
+def lbm_uses_tile_staging(h) -> int:
+    w = ctypes.c_int(0)
+    _check(load_library().lbm_uses_tile_staging(h, ctypes.byref(w)))
+    return w.value
+
+
+def lbm_set_stage_test(h, extra_tx_bytes: int, spin_limit: int):
+    _check(load_library().lbm_set_stage_test(h, int(extra_tx_bytes), int(spin_limit)))
 
 
 def lbm_set_graphs(h, enable: bool):

@@ -266,6 +266,8 @@ def test_pair_kernel_matches_single_node_kernel(mode, storage, shape):
     xf, xg = I.neq_noise(n3, 10), I.neq_noise(n3, 11)
     a = gpu_sim(p, storage)
     b = gpu_sim(p, storage)
+    for s in (a, b):
+        lbm.lbm_set_tile_staging(s.h, False)
     lbm.lbm_set_pairing(a.h, mode)
     lbm.lbm_set_pairing(b.h, "off")
     with pytest.raises(lbm.LbmError):
