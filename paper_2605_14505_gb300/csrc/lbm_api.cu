@@ -143,11 +143,19 @@ bool uses_pairs(const lbm_ctx* h, int odd)
     return wanted && h->ks->step2[h->p.forcing][0] != nullptr && (h->p.nx % 2) == 0;
 }
 
+// Default launch shape, from a sweep of the candidate shapes at 256^3: the
+// two-nodes-per-thread kernel runs best in 128-thread blocks of 64 x 2 (four
+// 128-register blocks per SM), the one-node kernels in blocks of one row of
+// 256 threads for D3Q27xD3Q19 and 128 for the smaller pairs.
 void default_block(lbm_ctx* h)
 {
-    const int xunits = uses_pairs(h, 0) ? h->p.nx / 2 : h->p.nx;
-    int bx = xunits >= 128 ? 128 : (xunits >= 64 ? 64 : 32);
-    int by = 256 / bx;
+    const bool pairs = uses_pairs(h, 0);
+    const int xunits = pairs ? h->p.nx / 2 : h->p.nx;
+    const int threads = pairs ? 128 : (h->q.qf + h->q.qg >= 46 ? 256 : 128);
+    const int want = pairs ? 64 : threads;
+    int bx = 32;
+    while (bx * 2 <= want && bx * 2 <= xunits) bx *= 2;
+    int by = threads / bx;
     while (by > 1 && by / 2 >= h->p.ny) by /= 2;
     h->bx = bx;
     h->by = by;

@@ -571,7 +571,7 @@ LBM_HD void collide_f_fast(float* h, const Macro& m, const Phys& ph)
         constexpr int ez = LF::ez(i);
         const float em = e_dot<LF, i>(mx, my, mz);
         float hs = fmaf((w * o2) * em, em, w * ob);
-        float ha = (w * o1) * em;
+        float ha = 0.f;          // forcing part of the odd term; the equilibrium part is (w o1) e.j
         if constexpr (FORCING == kGuo) {
             const float eu = em * m.irho;
             hs += gF * w * (ez != 0 ? (2.f * c2 * eu * (float)ez - c1 * vz) : -c1 * vz);
@@ -589,8 +589,13 @@ LBM_HD void collide_f_fast(float* h, const Macro& m, const Phys& ph)
             hs += w * m.rho * ps;
             if constexpr (ez != 0) ha += w * c1 * (float)ez * m.Fz;
         }
-        h[i] = fmaf(cm, h[i], hs + ha);
-        h[j] = fmaf(cm, h[j], hs - ha);
+        float hp = hs, hm = hs;
+        if constexpr (FORCING != kShanChen) {
+            hp = hs + ha;
+            hm = hs - ha;
+        }
+        h[i] = fmaf(cm, h[i], fmaf(w * o1, em, hp));
+        h[j] = fmaf(cm, h[j], fmaf(-(w * o1), em, hm));
     });
 }
 
@@ -617,9 +622,8 @@ LBM_HD void collide_g_fast(float* k, const Macro& m, const Phys& ph)
         constexpr float w = LG::w(i);
         const float eu = e_dot<LG, i>(m.ux, m.uy, m.uz);
         const float ks = fmaf((w * a2) * eu, eu, w * obs);
-        const float ka = (w * a1) * eu;
-        k[i] = fmaf(cm, k[i], ks + ka);
-        k[i + 1] = fmaf(cm, k[i + 1], ks - ka);
+        k[i] = fmaf(cm, k[i], fmaf(w * a1, eu, ks));
+        k[i + 1] = fmaf(cm, k[i + 1], fmaf(-(w * a1), eu, ks));
     });
 }
 
