@@ -325,8 +325,8 @@ def sweep_specs():
 
 
 def run_batch_sweep(args, peak):
-    """All 64 instances advanced together for 2000 steps (persistent
-    cooperative launches or graph-replayed per-step launches, tile shape and
+    """All 64 instances advanced together for 2000 steps (graph-replayed
+    per-variant launches or persistent cooperative launches, tile shape and
     driver picked by the library's autotuner). Aggregate MLUPS and the HBM
     roofline fraction of the whole batch."""
     import numpy as np
@@ -358,7 +358,7 @@ def run_batch_sweep(args, peak):
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "bytes_per_step": nbytes},
             "driver": "persistent" if cfg["mode"] == 0 else "per_step", "tile": [cfg["bx"], cfg["by"]],
-            "grid": cfg["grid"], "autotune_ms_per_step": round(tuned_ms, 4),
+            ("grid" if cfg["mode"] == 0 else "tiles"): cfg["grid"], "autotune_ms_per_step": round(tuned_ms, 4),
             "all_finite": all(np.isfinite(d["Ek"]) for d in diags), "timing": "host wall clock around 2000 steps"}
 
 
@@ -424,6 +424,20 @@ def run_ncu_case(args):
 
     from paper_2605_14505_gb300 import lbm
 
+    if args.ncu_case == "batch":
+        # the 64-instance sweep, persistent driver, `ncu_steps` steps per launch
+        specs = sweep_specs()
+        params = [lbm.lbm_params_from_physics(n, n, n, pair, f, Re, Fr, 1.0, U0) for n, pair, f, Re, Fr in specs]
+        b = lbm.lbm_batch_create(params)
+        lbm.lbm_batch_set_mode(b, "persistent", args.ncu_steps)
+        lbm.lbm_batch_set_block(b, 32, 8)
+        lbm.lbm_batch_init_tgv(b, seed=1, noise_amp=1e-3)
+        lbm.lbm_batch_step(b, 3 * args.ncu_steps)
+        lbm.lbm_batch_synchronize(b)
+        lbm.lbm_batch_destroy(b)
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": "batch", "steps": 3 * args.ncu_steps, "sources": source_fingerprint()}))
+        return
     storage, pair = args.ncu_case, PAIR
     if args.ncu_case.startswith("19x7"):
         storage, pair = ("fp16" if args.ncu_case.endswith("fp16") else "fp32"), "19x7"
@@ -450,7 +464,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched sweep")
-    ap.add_argument("--ncu-case", choices=["fp32", "fp16", "bf16", "19x7", "19x7-fp16"], default=None,
+    ap.add_argument("--ncu-case", choices=["fp32", "fp16", "bf16", "19x7", "19x7-fp16", "batch"], default=None,
                     help="run a small profiling case instead of the benchmark")
     ap.add_argument("--ncu-n", type=int, default=128)
     ap.add_argument("--ncu-steps", type=int, default=6)

@@ -287,11 +287,14 @@ int lbm_destroy(lbm_handle h);
 /* ---- Batched instances -------------------------------------------------
  * A parameter sweep of the paper's kind (Sections 3.2-3.6: stencil pairs,
  * forcing schemes, Froude numbers, resolutions) as many independent periodic
- * lattices advanced by one launch per step, or by one persistent cooperative
- * launch per `steps_per_launch` steps with a bounded grid barrier between
- * steps. Instances may differ in size, pair (D3Q27xD3Q19, D3Q19xD3Q7),
- * forcing and parameters; storage is FP32. Each instance's arithmetic is the
- * single-lattice update's. */
+ * lattices. Two drivers: per step, one launch per (pair, forcing) variant
+ * over that variant's tiles, replayed from a CUDA graph of 64 steps in which
+ * each variant's chain of steps is its own branch (variants share no
+ * instance, so the branches overlap); or one persistent cooperative launch
+ * per `steps_per_launch` steps over all tiles with a bounded grid barrier
+ * between steps. Instances may differ in size, pair (D3Q27xD3Q19,
+ * D3Q19xD3Q7), forcing and parameters; storage is FP32. Each instance's
+ * arithmetic is the single-lattice update's. */
 typedef struct lbm_batch_ctx* lbm_batch;
 
 enum lbm_batch_mode { LBM_BATCH_PERSISTENT = 0, LBM_BATCH_PER_STEP = 1 };
@@ -340,8 +343,10 @@ int lbm_batch_synchronize(lbm_batch b);
  * lbm_batch_synchronize; LBM_ENONFINITE if any instance has NaN/Inf). */
 int lbm_batch_diagnostics(lbm_batch b, lbm_diag* out);
 
-/* Time every tile shape and both modes (reps step pairs each, CUDA events)
- * and keep the fastest; the instances' state is saved and restored.
+/* Time every tile shape and both modes and keep the fastest: for each
+ * candidate one warm-up span, then reps spans timed with CUDA events, a span
+ * being one 64-step graph (per-step mode) or one persistent launch of
+ * steps_per_launch steps. The instances' state is saved and restored.
  * best_ms_per_step may be NULL. */
 int lbm_batch_autotune(lbm_batch b, int reps, double* best_ms_per_step);
 

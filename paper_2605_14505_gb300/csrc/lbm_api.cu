@@ -2,6 +2,7 @@
 // CUDA-graph replay of the AA step pair, diagnostics, autotuning.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1049,6 +1050,12 @@ struct lbm_batch_ctx {
     uint16_t* d_tile = nullptr;
     unsigned* d_sync = nullptr;
     uint32_t ntiles = 0;
+    uint32_t vbeg[8] = {}, vend[8] = {};   // tiles of each (pair, forcing) variant
+    // per-variant streams and events: the captured graph runs each variant's
+    // chain of steps as its own branch (variants share no instance)
+    cudaStream_t vstream[8] = {};
+    cudaEvent_t vjoin[8] = {};
+    cudaEvent_t vfork = nullptr;
     int bx = 32, by = 8;
     int mode = LBM_BATCH_PERSISTENT;
     int chunk = 100;
@@ -1076,7 +1083,14 @@ int batch_build_tiles(lbm_batch_ctx* b)
     std::vector<BatchInstance> hi(b->inst.size());
     std::vector<uint16_t> tiles;
     uint32_t t0 = 0;
-    for (size_t i = 0; i < b->inst.size(); ++i) {
+    // tiles listed variant by variant, so that each per-variant launch covers one range
+    std::vector<size_t> order(b->inst.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c) {
+        return 4 * b->inst[a]->p.pair + b->inst[a]->p.forcing < 4 * b->inst[c]->p.pair + b->inst[c]->p.forcing;
+    });
+    for (int v = 0; v < 8; ++v) b->vbeg[v] = b->vend[v] = 0;
+    for (size_t i : order) {
         lbm_ctx* h = b->inst[i];
         BatchInstance& I = hi[i];
         I.f = f_ptr(h);
@@ -1090,7 +1104,10 @@ int batch_build_tiles(lbm_batch_ctx* b)
         const uint64_t n = (uint64_t)I.tx * I.ty * (uint64_t)h->p.nz;
         if ((uint64_t)t0 + n > 0xffffffffull) return fail(LBM_EINVAL, "batch tile count exceeds 2^32");
         tiles.insert(tiles.end(), (size_t)n, (uint16_t)i);
+        const int v = I.variant;
+        if (b->vend[v] == b->vbeg[v]) b->vbeg[v] = t0;
         t0 += (uint32_t)n;
+        b->vend[v] = t0;
     }
     b->ntiles = t0;
     if (b->d_inst) cudaFree(b->d_inst);
@@ -1122,6 +1139,8 @@ BatchArgs batch_args(const lbm_batch_ctx* b, int steps, int odd0, unsigned grid)
     a.inst = b->d_inst;
     a.tile_inst = b->d_tile;
     a.ntiles = b->ntiles;
+    a.tile_begin = 0;
+    a.tile_end = b->ntiles;
     a.steps = steps;
     a.odd0 = odd0;
     a.sync = b->d_sync;
@@ -1130,12 +1149,41 @@ BatchArgs batch_args(const lbm_batch_ctx* b, int steps, int odd0, unsigned grid)
     return a;
 }
 
+cudaError_t batch_launch_variant(lbm_batch_ctx* b, int v, int odd, cudaStream_t s)
+{
+    const uint32_t n = b->vend[v] - b->vbeg[v];
+    if (n == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)(n < (uint32_t)(b->num_sms * 64) ? n : b->num_sms * 64);
+    BatchArgs a = batch_args(b, 1, odd, grid);
+    a.tile_begin = b->vbeg[v];
+    a.tile_end = b->vend[v];
+    void* args[] = {&a};
+    return cudaLaunchKernel(batch_variant_kernel(v, odd), dim3(grid), dim3(b->bx, b->by), args, 0, s);
+}
+
 cudaError_t batch_launch_step(lbm_batch_ctx* b, int odd, cudaStream_t s)
 {
-    const unsigned grid = (unsigned)(b->ntiles < (uint32_t)(b->num_sms * 64) ? b->ntiles : b->num_sms * 64);
-    BatchArgs a = batch_args(b, 1, odd, grid);
-    void* args[] = {&a};
-    return cudaLaunchKernel(batch_step_kernel(odd), dim3(grid), dim3(b->bx, b->by), args, 0, s);
+    for (int v = 0; v < 8; ++v) {
+        cudaError_t e = batch_launch_variant(b, v, odd, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Records `steps` steps (from the natural layout) into the capture running on
+// b->stream: each variant's chain on its own stream, forked from and joined
+// back to b->stream.
+cudaError_t batch_capture_steps(lbm_batch_ctx* b, int steps)
+{
+    cudaError_t e = cudaEventRecord(b->vfork, b->stream);
+    for (int v = 0; v < 8 && e == cudaSuccess; ++v) {
+        if (b->vend[v] == b->vbeg[v]) continue;
+        e = cudaStreamWaitEvent(b->vstream[v], b->vfork, 0);
+        for (int s = 0; s < steps && e == cudaSuccess; ++s) e = batch_launch_variant(b, v, s & 1, b->vstream[v]);
+        if (e == cudaSuccess) e = cudaEventRecord(b->vjoin[v], b->vstream[v]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->vjoin[v], 0);
+    }
+    return e;
 }
 
 cudaError_t batch_launch_persistent(lbm_batch_ctx* b, int steps, int odd, cudaStream_t s)
@@ -1189,6 +1237,15 @@ int lbm_batch_create(lbm_batch* out, const lbm_params* params, int count)
         return fail(LBM_ECUDA, "stream creation failed");
     }
     b->own_stream = true;
+    bool streams_ok = cudaEventCreateWithFlags(&b->vfork, cudaEventDisableTiming) == cudaSuccess;
+    for (int v = 0; v < 8 && streams_ok; ++v) {
+        streams_ok = cudaStreamCreateWithFlags(&b->vstream[v], cudaStreamNonBlocking) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&b->vjoin[v], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!streams_ok) {
+        cudaGetLastError();
+        rc = fail(LBM_ECUDA, "batch stream or event creation failed");
+    }
     for (int i = 0; i < count && rc == LBM_OK; ++i) {
         lbm_handle h = nullptr;
         rc = lbm_create_params(&h, &params[i]);
@@ -1307,7 +1364,7 @@ int lbm_batch_step(lbm_batch b, int64_t nsteps)
                 cudaGraph_t g = nullptr;
                 cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
                 if (e == cudaSuccess) {
-                    for (int s = 0; s < kBatchGraphSteps && e == cudaSuccess; ++s) e = batch_launch_step(b, s & 1, b->stream);
+                    e = batch_capture_steps(b, kBatchGraphSteps);
                     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
                     if (e == cudaSuccess) e = e2;
                 }
@@ -1374,7 +1431,7 @@ int lbm_batch_autotune(lbm_batch b, int reps, double* best_ms_per_step)
         }
         cudaMemcpyAsync(backup[i], b->inst[i]->store, b->inst[i]->store_bytes, cudaMemcpyDeviceToDevice, b->stream);
     }
-    static const int cand[][2] = {{16, 8}, {16, 16}, {32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {128, 2}};
+    static const int cand[][2] = {{16, 8}, {32, 2}, {32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {128, 2}};
     const int save_bx = b->bx, save_by = b->by, save_mode = b->mode, save_odd = b->odd;
     const int64_t save_step = b->step;
     double best = 1e300;
@@ -1387,16 +1444,19 @@ int lbm_batch_autotune(lbm_batch b, int reps, double* best_ms_per_step)
         b->by = c[1];
         if ((rc = batch_build_tiles(b))) break;
         for (int mode = 0; mode < 2 && rc == LBM_OK; ++mode) {
+            // time whole graph chunks (per-step driver) and whole launches
+            // (persistent driver), as lbm_batch_step runs them
             b->mode = mode;
-            lbm_batch_step(b, 2);
+            const int64_t span = (mode == LBM_BATCH_PER_STEP) ? kBatchGraphSteps : b->chunk;
+            if ((rc = lbm_batch_step(b, span))) break;   // warm-up, builds the graph
             cudaEventRecord(e0, b->stream);
-            rc = lbm_batch_step(b, 2 * (int64_t)reps);
+            rc = lbm_batch_step(b, span * (int64_t)reps);
             cudaEventRecord(e1, b->stream);
             if (rc) break;
             if ((rc = lbm_batch_synchronize(b))) break;
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            const double per = ms / (2.0 * reps);
+            const double per = ms / (double)(span * reps);
             if (per < best) {
                 best = per;
                 bbx = c[0];
@@ -1449,6 +1509,11 @@ int lbm_batch_destroy(lbm_batch b)
     if (b->d_inst) cudaFree(b->d_inst);
     if (b->d_tile) cudaFree(b->d_tile);
     if (b->d_sync) cudaFree(b->d_sync);
+    for (int v = 0; v < 8; ++v) {
+        if (b->vstream[v]) cudaStreamDestroy(b->vstream[v]);
+        if (b->vjoin[v]) cudaEventDestroy(b->vjoin[v]);
+    }
+    if (b->vfork) cudaEventDestroy(b->vfork);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return LBM_OK;

@@ -5,7 +5,8 @@
 // z-plane; one global tile list covers every instance. A block updates whole
 // tiles; the (pair, forcing) variant is uniform over a tile, so the switch
 // below never diverges inside a block. Two drivers:
-//   k_batch_step<ODD>   one launch per time step (graph-captured by the host);
+//   k_batch_variant     per time step one launch per (pair, forcing) variant over
+//                       that variant's tiles (graph-captured by the host);
 //   k_batch_persistent  a cooperative launch that advances `steps` time steps,
 //                       with a grid-wide barrier between steps. Every wait of
 //                       the barrier is bounded: after `spin_limit` polls the
@@ -23,33 +24,51 @@ __device__ __forceinline__ void batch_node(const BatchInstance& I, int x, int y,
     update_node<P, FORCING, float, ODD>(I.f, I.g, I.geo, I.ph, x, y, z);
 }
 
-template <bool ODD>
-__device__ __forceinline__ void batch_tile(const BatchArgs& A, uint32_t t)
+// Tile t of the global list: its instance and this thread's node; false if
+// the node lies outside the instance (ragged tiles).
+__device__ __forceinline__ bool tile_node(const BatchArgs& A, uint32_t t, const BatchInstance*& inst, int& x, int& y,
+                                          int& z)
 {
     const BatchInstance& I = A.inst[A.tile_inst[t]];
+    inst = &I;
     const uint32_t lt = t - I.tile0;
     const uint32_t plane = I.tx * I.ty;
-    const int z = (int)(lt / plane);
+    z = (int)(lt / plane);
     const uint32_t r = lt - (uint32_t)z * plane;
-    const int x = (int)((r % I.tx) * blockDim.x + threadIdx.x);
-    const int y = (int)((r / I.tx) * blockDim.y + threadIdx.y);
-    if (x >= I.geo.nx || y >= I.geo.ny) return;
-    switch (I.variant) {
-    case 0: batch_node<Pair<27, 19>, kGuo, ODD>(I, x, y, z); break;
-    case 1: batch_node<Pair<27, 19>, kShanChen, ODD>(I, x, y, z); break;
-    case 2: batch_node<Pair<27, 19>, kEDM, ODD>(I, x, y, z); break;
-    case 3: batch_node<Pair<27, 19>, kHCZ, ODD>(I, x, y, z); break;
-    case 4: batch_node<Pair<19, 7>, kGuo, ODD>(I, x, y, z); break;
-    case 5: batch_node<Pair<19, 7>, kShanChen, ODD>(I, x, y, z); break;
-    case 6: batch_node<Pair<19, 7>, kEDM, ODD>(I, x, y, z); break;
-    default: batch_node<Pair<19, 7>, kHCZ, ODD>(I, x, y, z); break;
-    }
+    x = (int)((r % I.tx) * blockDim.x + threadIdx.x);
+    y = (int)((r / I.tx) * blockDim.y + threadIdx.y);
+    return x < I.geo.nx && y < I.geo.ny;
 }
 
 template <bool ODD>
-__global__ void __launch_bounds__(256) k_batch_step(BatchArgs A)
+__device__ __forceinline__ void batch_tile(const BatchArgs& A, uint32_t t)
 {
-    for (uint32_t t = blockIdx.x; t < A.ntiles; t += gridDim.x) batch_tile<ODD>(A, t);
+    const BatchInstance* I;
+    int x, y, z;
+    if (!tile_node(A, t, I, x, y, z)) return;
+    switch (I->variant) {
+    case 0: batch_node<Pair<27, 19>, kGuo, ODD>(*I, x, y, z); break;
+    case 1: batch_node<Pair<27, 19>, kShanChen, ODD>(*I, x, y, z); break;
+    case 2: batch_node<Pair<27, 19>, kEDM, ODD>(*I, x, y, z); break;
+    case 3: batch_node<Pair<27, 19>, kHCZ, ODD>(*I, x, y, z); break;
+    case 4: batch_node<Pair<19, 7>, kGuo, ODD>(*I, x, y, z); break;
+    case 5: batch_node<Pair<19, 7>, kShanChen, ODD>(*I, x, y, z); break;
+    case 6: batch_node<Pair<19, 7>, kEDM, ODD>(*I, x, y, z); break;
+    default: batch_node<Pair<19, 7>, kHCZ, ODD>(*I, x, y, z); break;
+    }
+}
+
+// Per-step driver: one launch per (pair, forcing) variant over that variant's
+// tiles, which the host lists contiguously. Without the other variants'
+// code the kernel fits three 256-thread blocks per SM, as k_step does.
+template <class P, int FORCING, bool ODD>
+__global__ void __launch_bounds__(256, 3) k_batch_variant(BatchArgs A)
+{
+    for (uint32_t t = A.tile_begin + blockIdx.x; t < A.tile_end; t += gridDim.x) {
+        const BatchInstance* I;
+        int x, y, z;
+        if (tile_node(A, t, I, x, y, z)) batch_node<P, FORCING, ODD>(*I, x, y, z);
+    }
 }
 
 // Grid-wide barrier for a cooperative launch. sync[0] counts arrivals,
@@ -104,9 +123,24 @@ __global__ void __launch_bounds__(256) k_batch_persistent(BatchArgs A)
     }
 }
 
-const void* batch_step_kernel(int odd)
+template <class P, int F>
+const void* variant_kernel(int odd)
 {
-    return odd ? (const void*)k_batch_step<true> : (const void*)k_batch_step<false>;
+    return odd ? (const void*)k_batch_variant<P, F, true> : (const void*)k_batch_variant<P, F, false>;
+}
+
+const void* batch_variant_kernel(int variant, int odd)
+{
+    switch (variant) {
+    case 0: return variant_kernel<Pair<27, 19>, kGuo>(odd);
+    case 1: return variant_kernel<Pair<27, 19>, kShanChen>(odd);
+    case 2: return variant_kernel<Pair<27, 19>, kEDM>(odd);
+    case 3: return variant_kernel<Pair<27, 19>, kHCZ>(odd);
+    case 4: return variant_kernel<Pair<19, 7>, kGuo>(odd);
+    case 5: return variant_kernel<Pair<19, 7>, kShanChen>(odd);
+    case 6: return variant_kernel<Pair<19, 7>, kEDM>(odd);
+    default: return variant_kernel<Pair<19, 7>, kHCZ>(odd);
+    }
 }
 
 const void* batch_persistent_kernel() { return (const void*)k_batch_persistent; }

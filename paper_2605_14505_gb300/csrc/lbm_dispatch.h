@@ -29,7 +29,7 @@ const void* diag_gradients_kernel();
 const void* diag_final_kernel();
 
 // Batched update (FP32 storage, D3Q27xD3Q19 and D3Q19xD3Q7, all forcings).
-const void* batch_step_kernel(int odd);
+const void* batch_variant_kernel(int variant, int odd);   // variant = 4 * pair + forcing
 const void* batch_persistent_kernel();
 
 }  // namespace lbm

@@ -236,6 +236,8 @@ struct BatchArgs {
     const BatchInstance* inst;
     const uint16_t* tile_inst;  // instance index of every tile
     uint32_t ntiles;
+    uint32_t tile_begin;        // per-variant launches: the variant's tiles [tile_begin, tile_end)
+    uint32_t tile_end;
     int steps;                  // time steps of one persistent launch
     int odd0;                   // AA layout parity at the start
     unsigned* sync;             // grid barrier: arrivals, generation, error flag
