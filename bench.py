@@ -140,6 +140,9 @@ class ClockSampler:
 
 
 def dist_setup():
+    """Rank layout from the torchrun environment; one process group per job
+    (NCCL with GPUs, gloo without), used only for barriers and the max-time
+    reduction: the replicas exchange no lattice data."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -147,8 +150,9 @@ def dist_setup():
         import torch
         import torch.distributed as dist
 
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return world, rank, local
 
 
@@ -165,9 +169,16 @@ def max_over_ranks(world, value: float) -> float:
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_mlups(units_per_rank: float, world: int, max_secs: float) -> float:
+    """Whole-job throughput: every rank's lattice-node updates over the slowest
+    rank's time (weak scaling: each replica does the same work)."""
+    return units_per_rank * world / max_secs / 1e6
 
 
 def run_gpu_arm(args):
@@ -225,8 +236,7 @@ def run_gpu_arm(args):
     secs, step_ms, diag_ms, d32 = timed(sim, args.steps, args.warmup)
     clk = clocks.stop()
     secs = max_over_ranks(world, secs)
-    updates = float(n3) * DIAG_EVERY * args.steps * world
-    value = updates / secs / 1e6
+    value = aggregate_mlups(float(n3) * DIAG_EVERY * args.steps, world, secs)
     achieved = bytes_per_node("fp32") * n3 / (step_ms * 1e-3) / 1e9
     sim.close()
 
@@ -235,7 +245,7 @@ def run_gpu_arm(args):
         s = make(storage)
         vsecs, vstep_ms, _, dv = timed(s, args.steps, args.warmup)
         vsecs = max_over_ranks(world, vsecs)
-        vmlups = float(n3) * DIAG_EVERY * args.steps * world / vsecs / 1e6
+        vmlups = aggregate_mlups(float(n3) * DIAG_EVERY * args.steps, world, vsecs)
         vach = bytes_per_node(storage) * n3 / (vstep_ms * 1e-3) / 1e9
         err = {k: abs(dv[k] - d32[k]) / abs(d32[k]) for k in ("Ek", "Ep", "eps_k", "eps_p")}
         variants[storage] = {
@@ -278,7 +288,7 @@ def run_gpu_arm(args):
     barrier(world)
     e2e_secs = max_over_ranks(world, time.perf_counter() - t)
     lbm.lbm_destroy(h)
-    e2e = {"value": round(float(n3) * DIAG_EVERY * args.steps * world / e2e_secs / 1e6, 1),
+    e2e = {"value": round(aggregate_mlups(float(n3) * DIAG_EVERY * args.steps, world, e2e_secs), 1),
            "unit": "MLUPS", "h2d_bytes_per_step": 5 * n3 * 8, "d2h_bytes_per_step": 11 * 8}
 
     batch = run_batch_sweep(args, peak) if not args.no_batch else None
