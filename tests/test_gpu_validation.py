@@ -1,0 +1,66 @@
+"""Unstratified Taylor-Green validation runs (Section 3.1: the TGV without
+buoyancy, G = 0, D3Q27 momentum stencil, Ma = 0.05, a Reynolds sweep), on the
+CUDA path against the FP64 oracle: the E_k and eps_k time series, E_p and the
+scalar staying exactly at rest, and the laminar energy budget
+-dE_k/dt = eps_k."""
+import numpy as np
+import pytest
+
+import stgv_inputs as I
+from paper_2605_14505_gb300 import lbm
+
+from _helpers import oracle_for
+
+pytestmark = pytest.mark.gpu
+
+MA = 0.05
+U0 = MA * np.sqrt(1.0 / 3.0)
+
+
+@pytest.mark.parametrize("Re", [100.0, 400.0, 1600.0, 3000.0])
+def test_unstratified_tgv_series_against_oracle(Re):
+    n, chunks, every = 32, 15, 20
+    p = lbm.lbm_params_from_physics(n, n, n, "27x19", "guo", Re, float("inf"), 1.0, U0)
+    assert p.G == 0.0 and p.beta == 0.0
+    rho, u, rp = I.tgv_fields(n, U0)
+    g = lbm.Simulation(p)
+    g.init_fields(rho, u, rp)
+    o = oracle_for(p)
+    o.init_fields(rho, u, rp)
+    sg, so = [], []
+    for _ in range(chunks):
+        g.step(every)
+        o.step(every)
+        sg.append(g.diagnostics())
+        so.append(o.diagnostics())
+    for key in ("Ek", "eps_k", "eps_k_curl"):
+        a = np.array([d[key] for d in sg])
+        b = np.array([d[key] for d in so])
+        assert np.max(np.abs(a - b) / np.abs(b)) < 1e-5, (key, np.max(np.abs(a - b) / np.abs(b)))
+    # without buoyancy rho' carries only the compression of the rho0 share of
+    # g^eq by div u (an O(Ma^2) acoustic signal), the same on both sides
+    a = np.array([d["Ep"] for d in sg])
+    b = np.array([d["Ep"] for d in so])
+    assert np.max(np.abs(a - b)) < 1e-4 * np.max(np.abs(b))
+    g.close()
+    o.close()
+
+
+def test_unstratified_tgv_laminar_energy_budget():
+    """At Re 100 the flow stays laminar on 48^3. Once the initial acoustic
+    transient (the uniform initial density) has decayed, the central time
+    difference of E_k equals the non-equilibrium eps_k within 3 %
+    (Eq. 2's energy balance without buoyancy)."""
+    n, U0_ = 48, U0
+    p = lbm.lbm_params_from_physics(n, n, n, "27x19", "guo", 100.0, float("inf"), 1.0, U0_)
+    g = lbm.Simulation(p)
+    g.init_fields(*I.tgv_fields(n, U0_))
+    g.step(600)
+    dt = 30
+    e = []
+    for _ in range(3):
+        e.append(g.diagnostics())
+        g.step(dt)
+    rate = -(e[2]["Ek"] - e[0]["Ek"]) / (2 * dt)
+    assert abs(rate / e[1]["eps_k"] - 1) < 0.03, (rate, e[1]["eps_k"])
+    g.close()
