@@ -328,3 +328,32 @@ def test_other_stencil_pairs(pair, forcing):
     dg, do = g.diagnostics(), o.diagnostics()
     for key in ("Ek", "Ep", "eps_k", "eps_p", "eps_k_curl"):
         assert abs(dg[key] - do[key]) <= 2e-5 * abs(do[key]) + 1e-14, (key, dg[key], do[key])
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (33, 5, 3), (7, 2, 9)])
+def test_16bit_odd_nx_one_node_kernel_against_oracle(storage, shape):
+    """Odd nx (no pairs) runs the one-node 16-bit kernel: two steps against the
+    oracle from the same 16-bit-representable populations, within two storage
+    roundings of the node scale (one per step)."""
+    N = 3e-3
+    p = lattice_params(*shape, "27x19", "sc", 0.53, 0.56, N * LAM, -N / LAM)
+    n3 = shape[0] * shape[1] * shape[2]
+    g = gpu_sim(p, storage)
+    rho, u, rp = I.random_fields(*shape, 21, 0.05, 0.01, 0.02 / LAM)
+    g.init_fields(rho, u, rp, I.neq_noise(n3, 22), I.neq_noise(n3, 23), 1e-3)
+    o = oracle_for(p)
+    f0, g0 = g.populations()
+    o.set_populations(f0[np.argsort(slot_map(27))], g0[np.argsort(slot_map(19))])
+    ulp = 2.0 ** -11 if storage == "fp16" else 2.0 ** -8
+    _, wf, _ = lbm.lbm_velocity_set(27)
+    _, wg, _ = lbm.lbm_velocity_set(19)
+    for _ in range(2):
+        g.step(1)
+        o.step(1)
+        fg, gg = g.populations()
+        fo, go = o.populations()
+        fo, go = fo[slot_map(27)], go[slot_map(19)]
+        df, dg = fo - wf[:, None], go - p.rho0 * wg[:, None]
+        assert np.max(np.abs(fg - fo)) <= 4 * ulp * np.max(np.abs(df)) + 2.0 ** -23
+        assert np.max(np.abs(gg - go)) <= 4 * ulp * np.max(np.abs(dg)) + 2.0 ** -23
