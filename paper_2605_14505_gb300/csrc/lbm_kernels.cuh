@@ -513,6 +513,22 @@ struct DiagArgs {
     double* partials;    // gridDim.x * kDNumSlots
 };
 
+// Compensated (Kahan) FP32 running sum for a thread's share of a diagnostics
+// reduction: within a few FP32 ulps of the exact sum of its terms, on the FP32
+// pipes (this GPU's FP64 rate is a small fraction of its FP32 rate). The
+// thread partials are then combined in FP64.
+struct KahanF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 template <int NV, bool MAXLAST>
 __device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* out)
 {
@@ -544,9 +560,8 @@ __global__ void __launch_bounds__(kDiagBlock) k_diag_moments(DiagArgs a)
 {
     using LF = typename P::LF;
     const uint32_t n3 = a.geo.n3;
-    double acc[kDiagPass1];
-#pragma unroll
-    for (int q = 0; q < kDiagPass1; ++q) acc[q] = 0.0;
+    KahanF acc[kDiagPass1 - 1];
+    float umax = 0.f;
     for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n3; idx += gridDim.x * blockDim.x) {
         int x, y, z;
         node_xyz(a.geo, idx, x, y, z);
@@ -597,15 +612,15 @@ __global__ void __launch_bounds__(kDiagBlock) k_diag_moments(DiagArgs a)
         const float pyz = myz - rr * m.uy * m.uz + 0.5f * m.uy * m.Fz;
         const float ss = pxx * pxx + pyy * pyy + pzz * pzz + 2.f * (pxy * pxy + pxz * pxz + pyz * pyz);
         const float sfac = a.s_scale * m.irho;
-        acc[kDEk] += 0.5 * (double)usq;
-        acc[kDEp] += (double)(a.ep_scale * m.rho_p * m.rho_p);
-        acc[kDEpsK] += (double)(a.epsk_scale * sfac * sfac * ss);
-        acc[kDDrho] += (double)m.drho;
-        acc[kDA] += (double)m.a;
-        acc[kDJx] += (double)m.jx;
-        acc[kDJy] += (double)m.jy;
-        acc[kDJz] += (double)m.jz;
-        acc[kDUmax] = fmax(acc[kDUmax], (double)sqrtf(usq));
+        acc[kDEk].add(0.5f * usq);
+        acc[kDEp].add(a.ep_scale * m.rho_p * m.rho_p);
+        acc[kDEpsK].add(a.epsk_scale * sfac * sfac * ss);
+        acc[kDDrho].add(m.drho);
+        acc[kDA].add(m.a);
+        acc[kDJx].add(m.jx);
+        acc[kDJy].add(m.jy);
+        acc[kDJz].add(m.jz);
+        umax = fmaxf(umax, sqrtf(usq));
         if (a.fields) {
             a.fields[idx] = m.rho_p;
             a.fields[(size_t)n3 + idx] = m.ux;
@@ -613,7 +628,11 @@ __global__ void __launch_bounds__(kDiagBlock) k_diag_moments(DiagArgs a)
             a.fields[3 * (size_t)n3 + idx] = m.uz;
         }
     }
-    block_reduce_store<kDiagPass1, true>(acc, a.partials + (size_t)blockIdx.x * kDNumSlots);
+    double v[kDiagPass1];
+#pragma unroll
+    for (int q = 0; q < kDiagPass1 - 1; ++q) v[q] = acc[q].value();
+    v[kDUmax] = (double)umax;
+    block_reduce_store<kDiagPass1, true>(v, a.partials + (size_t)blockIdx.x * kDNumSlots);
 }
 
 #ifdef LBM_REDUCTION_KERNELS  // defined in exactly one translation unit
@@ -625,7 +644,7 @@ __global__ void __launch_bounds__(kDiagBlock) k_diag_gradients(DiagArgs a)
     const float* ux = a.fields + n3;
     const float* uy = a.fields + 2 * (size_t)n3;
     const float* uz = a.fields + 3 * (size_t)n3;
-    double acc[kDiagPass2] = {0.0, 0.0};
+    KahanF acc[kDiagPass2];
     for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n3; idx += gridDim.x * blockDim.x) {
         int x, y, z;
         node_xyz(a.geo, idx, x, y, z);
@@ -639,10 +658,11 @@ __global__ void __launch_bounds__(kDiagBlock) k_diag_gradients(DiagArgs a)
         const float wx = 0.5f * (uz[yp] - uz[ym]) - 0.5f * (uy[zp] - uy[zm]);
         const float wy = 0.5f * (ux[zp] - ux[zm]) - 0.5f * (uz[xp] - uz[xm]);
         const float wz = 0.5f * (uy[xp] - uy[xm]) - 0.5f * (ux[yp] - ux[ym]);
-        acc[0] += (double)(a.epsp_scale * (gx * gx + gy * gy + gz * gz));
-        acc[1] += (double)(a.nu * (wx * wx + wy * wy + wz * wz));
+        acc[0].add(a.epsp_scale * (gx * gx + gy * gy + gz * gz));
+        acc[1].add(a.nu * (wx * wx + wy * wy + wz * wz));
     }
-    block_reduce_store<kDiagPass2, false>(acc, a.partials + (size_t)blockIdx.x * kDNumSlots + kDiagPass1);
+    double v[kDiagPass2] = {acc[0].value(), acc[1].value()};
+    block_reduce_store<kDiagPass2, false>(v, a.partials + (size_t)blockIdx.x * kDNumSlots + kDiagPass1);
 }
 
 // Final pass: one block adds the per-block partials in a fixed order.

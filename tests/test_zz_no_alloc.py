@@ -7,9 +7,12 @@ synchronisation that cudaMalloc/cudaFree imply while other streams are busy,
 or a process that is out of headroom. Its scratch is a fixed array compiled
 into the library, shared by every call, so this test calls it twice in a row
 (with steps in between) and each time compares it with lbm_diagnostics on the
-same state, within 1e-10 relative (the two sum the same FP32 per-node values in
-a different FP64 order). This file is collected last so that a failure here
-leaves every other test already run.
+same state. The two sum the same FP32 per-node values over different thread
+partitions (compensated FP32 within a thread, FP64 across threads): energies,
+dissipation, mass and the maximum speed agree within 1e-10 relative; the total
+momentum, a sum of O(1e-2) terms that cancels to O(1e-1), within 1e-6
+absolute (5e-10 of the sum of |j| over the 48^3 nodes). This file is
+collected last so that a failure here leaves every other test already run.
 """
 import math
 
@@ -39,7 +42,7 @@ def test_noalloc_diagnostics_match_two_calls_in_a_row():
         for key in KEYS:
             assert _close(got[key], ref[key]), (key, got[key], ref[key])
         for key in ("mom_x", "mom_y", "mom_z"):
-            assert _close(got[key], ref[key], abs_=1e-13), (key, got[key], ref[key])
+            assert _close(got[key], ref[key], abs_=1e-6), (key, got[key], ref[key])
         assert math.isnan(got["eps_p"]) and math.isnan(got["eps_k_curl"])
     sim.close()
 
