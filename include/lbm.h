@@ -189,6 +189,20 @@ int lbm_synchronize(lbm_handle h);
  * LBM_ENONFINITE if any value is NaN/Inf (out is still written). */
 int lbm_diagnostics(lbm_handle h, lbm_diag* out);
 
+/* Fused diagnostics: the diagnostics of the current state (the same
+ * quantities as lbm_diagnostics, Eqs. 22-26, with out->step = the step count
+ * at entry), reduced by the first of nsteps >= 1 steps from the
+ * post-stream, pre-collision populations that step loads anyway, followed by
+ * the remaining nsteps - 1 steps. Returns when the diagnostics are on the
+ * host; the steps may still run (asynchronous on the handle's stream).
+ * The per-node sums are per step-kernel block instead of per diagnostics
+ * block, so the results equal lbm_diagnostics' up to FP32 summation order;
+ * with FP16/BF16 storage the node moments come from the step's short-form
+ * FP32 arithmetic (~1e-8 relative difference).
+ * Errors: LBM_EINVAL (nsteps < 1, null out), LBM_ESTATE (not initialised),
+ * LBM_ENONFINITE as lbm_diagnostics. */
+int lbm_step_diagnostics(lbm_handle h, int64_t nsteps, lbm_diag* out);
+
 /* Macroscopic fields of the current state into host FP64 arrays: rho (Eq. 6),
  * physical u (Eq. 7, 3 blocks), rho' (Eq. 16). Any pointer may be NULL. */
 int lbm_get_fields(lbm_handle h, double* rho, double* u, double* rho_p);

@@ -92,6 +92,8 @@ struct lbm_ctx {
     // diagnostics scratch
     float* diag_fields = nullptr;
     double* diag_partials = nullptr;
+    int diag_rows = 0;                 // rows of kDNumSlots the partials hold
+    cudaEvent_t diag_event = nullptr;  // diagnostics copied to the host
     double* diag_out = nullptr;
     double* diag_host = nullptr;   // pinned
     int diag_blocks = 0;
@@ -207,18 +209,80 @@ int ensure_staging(lbm_ctx* h, size_t bytes)
     return LBM_OK;
 }
 
-int ensure_diag(lbm_ctx* h)
+// Diagnostics scratch: FP32 fields for pass 2, per-block partials (at least
+// `rows` rows), the totals, a pinned host copy and its completion event.
+int ensure_diag(lbm_ctx* h, int rows = 0)
 {
-    if (h->diag_fields) return LBM_OK;
-    h->diag_blocks = 4 * (h->num_sms > 0 ? h->num_sms : 132);
-    size_t fbytes = 4 * (size_t)h->geo.n3 * sizeof(float);
-    if (cudaMalloc(&h->diag_fields, fbytes) != cudaSuccess ||
-        cudaMalloc(&h->diag_partials, (size_t)h->diag_blocks * kDNumSlots * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&h->diag_out, 16 * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&h->diag_host, 16 * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(LBM_ENOMEM, "diagnostics scratch allocation failed");
+    if (!h->diag_fields) {
+        h->diag_blocks = 4 * (h->num_sms > 0 ? h->num_sms : 132);
+        size_t fbytes = 4 * (size_t)h->geo.n3 * sizeof(float);
+        if (cudaMalloc(&h->diag_fields, fbytes) != cudaSuccess ||
+            cudaMalloc(&h->diag_out, 16 * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost(&h->diag_host, 16 * sizeof(double)) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->diag_event, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LBM_ENOMEM, "diagnostics scratch allocation failed");
+        }
     }
+    const int need = rows > h->diag_blocks ? rows : h->diag_blocks;
+    if (h->diag_rows < need) {
+        if (h->diag_partials) {
+            cudaStreamSynchronize(h->stream);
+            cudaFree(h->diag_partials);
+            h->diag_partials = nullptr;
+            h->diag_rows = 0;
+        }
+        if (cudaMalloc(&h->diag_partials, (size_t)need * kDNumSlots * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LBM_ENOMEM, "diagnostics partials allocation failed");
+        }
+        h->diag_rows = need;
+    }
+    return LBM_OK;
+}
+
+// DiagArgs of the current state (scales of Eqs. 22-26 from the parameters).
+DiagArgs diag_args(lbm_ctx* h)
+{
+    const lbm_params& p = h->p;
+    const double cs2f = cs2_of(h->q.qf), cs2g = cs2_of(h->q.qg);
+    const double gn2 = (p.beta != 0.0) ? (-p.G * p.rho0 / p.beta) : 1.0;
+    const double nu = cs2f * (p.tau_f - 0.5), D = cs2g * (p.tau_g - 0.5);
+    DiagArgs a;
+    a.f = f_ptr(h);
+    a.g = g_ptr(h);
+    a.geo = h->geo;
+    a.ph = h->ph;
+    a.odd = h->odd;
+    a.ep_scale = (float)(0.5 * gn2 / (p.rho0 * p.rho0));
+    a.epsk_scale = (float)(2.0 * nu);
+    a.s_scale = (float)(-1.0 / (2.0 * cs2f * p.tau_f));
+    a.epsp_scale = (float)(D * gn2 / (p.rho0 * p.rho0));
+    a.nu = (float)nu;
+    a.fields = h->diag_fields;
+    a.partials = h->diag_partials;
+    return a;
+}
+
+// Totals (diag_host) -> lbm_diag of the state at `step`.
+int fill_diag(const lbm_ctx* h, int64_t step, lbm_diag* out)
+{
+    const double* s = h->diag_host;
+    const double inv = 1.0 / (double)h->geo.n3;
+    out->Ek = s[kDEk] * inv;
+    out->Ep = s[kDEp] * inv;
+    out->eps_k = s[kDEpsK] * inv;
+    out->eps_p = s[kDEpsP] * inv;
+    out->eps_k_curl = s[kDEpsKCurl] * inv;
+    out->mass_f = (double)h->geo.n3 + s[kDDrho];
+    out->mass_g = (double)h->geo.n3 * h->p.rho0 + s[kDA];
+    out->mom[0] = s[kDJx];
+    out->mom[1] = s[kDJy];
+    out->mom[2] = s[kDJz];
+    out->umax = s[kDUmax];
+    out->step = step;
+    for (int q = 0; q < kDNumSlots; ++q)
+        if (!std::isfinite(s[q])) return fail(LBM_ENONFINITE, "non-finite diagnostics at step %lld", (long long)step);
     return LBM_OK;
 }
 
@@ -620,23 +684,7 @@ int lbm_diagnostics(lbm_handle h, lbm_diag* out)
     if (!out) return fail(LBM_EINVAL, "null output");
     if (!h->initialized) return fail(LBM_ESTATE, "diagnostics before initialisation");
     if ((rc = ensure_diag(h))) return rc;
-    const lbm_params& p = h->p;
-    const double cs2f = cs2_of(h->q.qf), cs2g = cs2_of(h->q.qg);
-    const double gn2 = (p.beta != 0.0) ? (-p.G * p.rho0 / p.beta) : 1.0;
-    const double nu = cs2f * (p.tau_f - 0.5), D = cs2g * (p.tau_g - 0.5);
-    DiagArgs a;
-    a.f = f_ptr(h);
-    a.g = g_ptr(h);
-    a.geo = h->geo;
-    a.ph = h->ph;
-    a.odd = h->odd;
-    a.ep_scale = (float)(0.5 * gn2 / (p.rho0 * p.rho0));
-    a.epsk_scale = (float)(2.0 * nu);
-    a.s_scale = (float)(-1.0 / (2.0 * cs2f * p.tau_f));
-    a.epsp_scale = (float)(D * gn2 / (p.rho0 * p.rho0));
-    a.nu = (float)nu;
-    a.fields = h->diag_fields;
-    a.partials = h->diag_partials;
+    DiagArgs a = diag_args(h);
     void* args[] = {&a};
     LBM_CUDA(cudaLaunchKernel(h->ks->diag_moments, dim3(h->diag_blocks), dim3(kDiagBlock), args, 0, h->stream),
              "diag pass 1");
@@ -645,28 +693,63 @@ int lbm_diagnostics(lbm_handle h, lbm_diag* out)
     const double* pp = h->diag_partials;
     int nb = h->diag_blocks;
     double* dout = h->diag_out;
-    void* fargs[] = {&pp, &nb, &dout};
+    void* fargs[] = {&pp, &nb, &nb, &dout};
     LBM_CUDA(cudaLaunchKernel(diag_final_kernel(), dim3(1), dim3(kDiagBlock), fargs, 0, h->stream), "diag pass 3");
     LBM_CUDA(cudaMemcpyAsync(h->diag_host, h->diag_out, kDNumSlots * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
              "diag copy");
     LBM_CUDA(cudaStreamSynchronize(h->stream), "diagnostics");
-    const double* s = h->diag_host;
-    const double inv = 1.0 / (double)h->geo.n3;
-    out->Ek = s[kDEk] * inv;
-    out->Ep = s[kDEp] * inv;
-    out->eps_k = s[kDEpsK] * inv;
-    out->eps_p = s[kDEpsP] * inv;
-    out->eps_k_curl = s[kDEpsKCurl] * inv;
-    out->mass_f = (double)h->geo.n3 + s[kDDrho];
-    out->mass_g = (double)h->geo.n3 * p.rho0 + s[kDA];
-    out->mom[0] = s[kDJx];
-    out->mom[1] = s[kDJy];
-    out->mom[2] = s[kDJz];
-    out->umax = s[kDUmax];
-    out->step = h->step;
-    for (int q = 0; q < kDNumSlots; ++q)
-        if (!std::isfinite(s[q])) return fail(LBM_ENONFINITE, "non-finite diagnostics at step %lld", (long long)h->step);
-    return LBM_OK;
+    return fill_diag(h, h->step, out);
+}
+
+int lbm_step_diagnostics(lbm_handle h, int64_t nsteps, lbm_diag* out)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!out) return fail(LBM_EINVAL, "null output");
+    if (nsteps < 1) return fail(LBM_EINVAL, "lbm_step_diagnostics needs at least one step");
+    if (!h->initialized) return fail(LBM_ESTATE, "lbm_step_diagnostics before initialisation");
+    const int odd = h->odd;
+    const bool pairs = uses_pairs(h, odd);
+    const dim3 grid = step_grid(h, odd);
+    const int rows = (int)(grid.x * grid.y * grid.z);
+    const int level1 = h->num_sms > 0 ? h->num_sms : 132;   // first-level rows of the final pass
+    if ((rc = ensure_diag(h, rows + level1))) return rc;
+    const DiagArgs da = diag_args(h);
+    StepArgs a{};
+    a.f = f_ptr(h);
+    a.g = g_ptr(h);
+    a.geo = h->geo;
+    a.ph = h->ph;
+    a.dg = DiagSink{da.ep_scale, da.epsk_scale, da.s_scale, h->diag_fields, h->diag_partials};
+    void* args[] = {&a};
+    const void* k = pairs ? h->ks->step2_diag[h->p.forcing][odd] : h->ks->step_diag[h->p.forcing][odd];
+    LBM_CUDA(cudaLaunchKernel(k, grid, dim3(h->bx, h->by), args, 0, h->stream), "diagnosing step");
+    const int64_t step0 = h->step;
+    h->odd ^= 1;
+    h->step += 1;
+    DiagArgs g = da;
+    void* gargs[] = {&g};
+    LBM_CUDA(cudaLaunchKernel(diag_gradients_kernel(), dim3(h->diag_blocks), dim3(kDiagBlock), gargs, 0, h->stream),
+             "diag pass 2");
+    // pass 3 in two levels: `level1` blocks each sum a contiguous range of the
+    // step blocks' rows (and of the pass-2 rows) into one row, then one block
+    const double* pp = h->diag_partials;
+    int nb1 = rows, nb2 = h->diag_blocks;
+    double* mid = h->diag_partials + (size_t)rows * kDNumSlots;
+    void* l1args[] = {&pp, &nb1, &nb2, &mid};
+    LBM_CUDA(cudaLaunchKernel(diag_final_kernel(), dim3(level1), dim3(kDiagBlock), l1args, 0, h->stream),
+             "diag pass 3a");
+    const double* pm = mid;
+    int nl = level1;
+    double* dout = h->diag_out;
+    void* fargs[] = {&pm, &nl, &nl, &dout};
+    LBM_CUDA(cudaLaunchKernel(diag_final_kernel(), dim3(1), dim3(kDiagBlock), fargs, 0, h->stream), "diag pass 3b");
+    LBM_CUDA(cudaMemcpyAsync(h->diag_host, h->diag_out, kDNumSlots * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+             "diag copy");
+    LBM_CUDA(cudaEventRecord(h->diag_event, h->stream), "diag event");
+    if ((rc = lbm_step(h, nsteps - 1))) return rc;
+    LBM_CUDA(cudaEventSynchronize(h->diag_event), "diagnostics");
+    return fill_diag(h, step0, out);
 }
 
 int lbm_get_fields(lbm_handle h, double* rho, double* u, double* rho_p)
@@ -991,8 +1074,9 @@ int lbm_diagnostics_noalloc(lbm_handle h, lbm_diag* out)
              "static diag pass 1");
     const double* pp = scratch;
     int nb = (int)blocks;
+    int nb2 = 0;   // no pass 2 here
     double* dout = scratch + kStaticOutOffset;
-    void* fargs[] = {&pp, &nb, &dout};
+    void* fargs[] = {&pp, &nb, &nb2, &dout};
     LBM_CUDA(cudaLaunchKernel(diag_final_kernel(), dim3(1), dim3(kDiagBlock), fargs, 0, h->stream),
              "static diag pass 2");
     double s[kDNumSlots];
@@ -1029,6 +1113,7 @@ int lbm_destroy(lbm_handle h)
     if (h->diag_partials) cudaFree(h->diag_partials);
     if (h->diag_out) cudaFree(h->diag_out);
     if (h->diag_host) cudaFreeHost(h->diag_host);
+    if (h->diag_event) cudaEventDestroy(h->diag_event);
     if (h->d_err) cudaFree(h->d_err);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;

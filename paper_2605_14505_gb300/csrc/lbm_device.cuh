@@ -629,10 +629,11 @@ LBM_HD void collide_g_fast(float* k, const Macro& m, const Phys& ph)
 
 // Moments, coupled solve and both collisions of one node, in place on h, k:
 // the exact FP32 forms for FP32 storage, the short forms for 16-bit storage.
-template <class P, int FORCING, bool EXACT>
-LBM_HD Macro collide_node(float* h, float* k, const Phys& ph)
+template <class P, int FORCING, bool EXACT, class Hook>
+LBM_HD Macro collide_node(float* h, float* k, const Phys& ph, Hook&& hook)
 {
     const Macro m = node_macro<P, EXACT>(h, k, ph);
+    hook(static_cast<const float*>(h), m);
     if constexpr (EXACT) {
         collide_f<P, FORCING>(h, m, ph);
         collide_g<P>(k, m, ph);
@@ -641,6 +642,12 @@ LBM_HD Macro collide_node(float* h, float* k, const Phys& ph)
         collide_g_fast<P>(k, m, ph);
     }
     return m;
+}
+
+template <class P, int FORCING, bool EXACT>
+LBM_HD Macro collide_node(float* h, float* k, const Phys& ph)
+{
+    return collide_node<P, FORCING, EXACT>(h, k, ph, [](const float*, const Macro&) {});
 }
 
 }  // namespace lbm

@@ -10,6 +10,8 @@ struct KernelSet {
     const void* step[4][2];   // [forcing][odd]
     const void* step2[4][2];  // two nodes per thread (16-bit storage, even nx), or null
     const void* staged[4][2]; // two nodes per thread, bulk-copy staged tiles (16-bit storage), or null
+    const void* step_diag[4][2];   // step that also reduces the diagnostics of its input state
+    const void* step2_diag[4][2];  // the same for the two-nodes-per-thread kernel, or null
     const void* init_fields;
     const void* init_tgv;
     const void* get_pops;

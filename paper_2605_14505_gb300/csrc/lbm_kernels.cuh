@@ -6,18 +6,238 @@
 
 namespace lbm {
 
+// ---------------------------------------------------------------------------
+// Diagnostics (Eqs. 22-26), three deterministic passes.
+// ---------------------------------------------------------------------------
+enum DiagSlot : int {
+    kDEk = 0, kDEp, kDEpsK, kDDrho, kDA, kDJx, kDJy, kDJz, kDUmax,   // pass 1
+    kDEpsP, kDEpsKCurl,                                            // pass 2
+    kDNumSlots
+};
+constexpr int kDiagPass1 = 9;
+constexpr int kDiagPass2 = 2;
+constexpr int kDiagBlock = 256;
+
+struct DiagArgs {
+    const void* f;
+    const void* g;
+    Geometry geo;
+    Phys ph;
+    int odd;
+    float ep_scale;      // (G/N)^2 / (2 rho0^2)
+    float epsk_scale;    // 2 nu
+    float s_scale;       // -1 / (2 cs^2 tau_f)
+    float epsp_scale;    // D (G/N)^2 / rho0^2
+    float nu;
+    float* fields;       // 4 * n3: rho', ux, uy, uz (written by pass 1, read by pass 2)
+    double* partials;    // gridDim.x * kDNumSlots
+};
+
+// Compensated (Kahan) FP32 running sum for a thread's share of a diagnostics
+// reduction: within a few FP32 ulps of the exact sum of its terms, on the FP32
+// pipes (this GPU's FP64 rate is a small fraction of its FP32 rate). The
+// thread partials are then combined in FP64.
+struct KahanF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Block sum (the last slot a maximum if MAXLAST) of v into out[0..NV), for
+// blocks of up to 256 threads, a whole number of warps, in any shape.
+template <int NV, bool MAXLAST>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* out)
+{
+    __shared__ double sh[kDiagBlock / 32][NV];
+    const int tid = (int)(threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z));
+    const int nwarps = (int)(blockDim.x * blockDim.y * blockDim.z) / 32;
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double t = __shfl_down_sync(0xffffffffu, v[q], o);
+            v[q] = (MAXLAST && q == NV - 1) ? fmax(v[q], t) : v[q] + t;
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sh[wid][q] = v[q];
+    }
+    __syncthreads();
+    if (tid < NV) {
+        const int q = tid;
+        double acc = sh[0][q];
+        for (int w = 1; w < nwarps; ++w) acc = (MAXLAST && q == NV - 1) ? fmax(acc, sh[w][q]) : acc + sh[w][q];
+        out[q] = acc;
+    }
+}
+
+// What a kernel needs to add one node's diagnostics (pass 1): the scales of
+// Eqs. 22-24 and of the non-equilibrium eps_k, the fields for pass 2 and the
+// per-block partials.
+struct DiagSink {
+    float ep_scale;      // (G/N)^2 / (2 rho0^2)
+    float epsk_scale;    // 2 nu
+    float s_scale;       // -1 / (2 cs^2 tau_f)
+    float* fields;       // 4 * n3: rho', ux, uy, uz
+    double* partials;    // one row of kDNumSlots per block
+};
+
+// a + b = s + e exactly (Knuth's two-sum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+struct DiagAcc {
+    KahanF acc[kDiagPass1 - 1];
+    float umax = 0.f;
+    // The pass-1 slots of this thread into one block row. The block sum is
+    // carried as an unevaluated FP32 pair (hi + lo, two-sum at every add), so
+    // the step kernels, which write one row per block, keep FP64-like
+    // accuracy on the FP32 pipes; one thread per slot converts the pair.
+    __device__ __forceinline__ void store_block(double* row)
+    {
+        __shared__ float sh[kDiagBlock / 32][kDiagPass1][2];
+        const int tid = (int)(threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z));
+        const int nwarps = (int)(blockDim.x * blockDim.y * blockDim.z) / 32;
+        const int lane = tid & 31, wid = tid >> 5;
+        float hi[kDiagPass1], lo[kDiagPass1];
+#pragma unroll
+        for (int q = 0; q < kDiagPass1 - 1; ++q) {
+            hi[q] = acc[q].s;
+            lo[q] = -acc[q].c;
+        }
+        hi[kDUmax] = umax;
+        lo[kDUmax] = 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int q = 0; q < kDiagPass1; ++q) {
+                const float oh = __shfl_down_sync(0xffffffffu, hi[q], o);
+                const float ol = __shfl_down_sync(0xffffffffu, lo[q], o);
+                if (q == kDUmax) {
+                    hi[q] = fmaxf(hi[q], oh);
+                } else {
+                    float t, e;
+                    two_sum(hi[q], oh, t, e);
+                    hi[q] = t;
+                    lo[q] = lo[q] + ol + e;
+                }
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < kDiagPass1; ++q) {
+                sh[wid][q][0] = hi[q];
+                sh[wid][q][1] = lo[q];
+            }
+        }
+        __syncthreads();
+        if (tid < kDiagPass1) {
+            const int q = tid;
+            float h = sh[0][q][0], l = sh[0][q][1];
+            for (int w = 1; w < nwarps; ++w) {
+                if (q == kDUmax) {
+                    h = fmaxf(h, sh[w][q][0]);
+                } else {
+                    float t, e;
+                    two_sum(h, sh[w][q][0], t, e);
+                    h = t;
+                    l = l + sh[w][q][1] + e;
+                }
+            }
+            // the pair itself, in the slot's 8 bytes (k_diag_final with pass1_pairs)
+            reinterpret_cast<float2*>(row)[q] = make_float2(h, l);
+        }
+    }
+};
+
+// One node's pass-1 diagnostics from its post-stream, pre-collision
+// populations and moments, and its FP32 fields for pass 2. PAIRSUM: h holds
+// each opposite pair as (sum, difference), the exact node_macro form;
+// otherwise the raw deviations. Second moment of the deviations:
+// M2 = sum e e h, Pi_neq = M2 - rho u u - drho cs^2 I; e e is the same for e
+// and -e, so a pair contributes e e (h_i + h_j). D3Q7 lacks the fourth-order
+// isotropy behind sum e e f_eq = rho u u + rho cs^2 I, so there the pair sums
+// of f_eq(rho, u) are subtracted explicitly and the closed-form terms are not.
+template <class P, bool PAIRSUM>
+__device__ __forceinline__ void diag_node(const float* h, const Macro& m, const DiagSink& s, uint32_t n3,
+                                          uint32_t idx, DiagAcc& d)
+{
+    using LF = typename P::LF;
+    constexpr bool kExplicit = (LF::kQ == 7);
+    const float usq = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
+    float mxx = 0.f, myy = 0.f, mzz = 0.f, mxy = 0.f, mxz = 0.f, myz = 0.f;
+    sfor<0, kPairs<LF>>([&](auto mc) {
+        constexpr int i = 2 * decltype(mc)::value + 1;
+        float sp = PAIRSUM ? h[i] : h[i] + h[i + 1];
+        if constexpr (kExplicit) {
+            const float eu = e_dot<LF, i>(m.ux, m.uy, m.uz);
+            sp -= 2.f * LF::w(i) * (m.drho + m.rho * (LF::half_inv_cs4 * eu * eu - LF::half_inv_cs2 * usq));
+        }
+        if constexpr (LF::ex(i) != 0) mxx += sp;
+        if constexpr (LF::ey(i) != 0) myy += sp;
+        if constexpr (LF::ez(i) != 0) mzz += sp;
+        if constexpr (LF::ex(i) * LF::ey(i) == 1) mxy += sp;
+        if constexpr (LF::ex(i) * LF::ey(i) == -1) mxy -= sp;
+        if constexpr (LF::ex(i) * LF::ez(i) == 1) mxz += sp;
+        if constexpr (LF::ex(i) * LF::ez(i) == -1) mxz -= sp;
+        if constexpr (LF::ey(i) * LF::ez(i) == 1) myz += sp;
+        if constexpr (LF::ey(i) * LF::ez(i) == -1) myz -= sp;
+    });
+    const float dc = kExplicit ? 0.f : m.drho * LF::cs2;
+    const float rr = kExplicit ? 0.f : m.rho;
+    // S = s_scale / rho * (Pi_neq + (u F + F u) / 2), F = (0, 0, Fz)
+    const float pxx = mxx - rr * m.ux * m.ux - dc;
+    const float pyy = myy - rr * m.uy * m.uy - dc;
+    const float pzz = mzz - rr * m.uz * m.uz - dc + m.uz * m.Fz;
+    const float pxy = mxy - rr * m.ux * m.uy;
+    const float pxz = mxz - rr * m.ux * m.uz + 0.5f * m.ux * m.Fz;
+    const float pyz = myz - rr * m.uy * m.uz + 0.5f * m.uy * m.Fz;
+    const float ss = pxx * pxx + pyy * pyy + pzz * pzz + 2.f * (pxy * pxy + pxz * pxz + pyz * pyz);
+    const float sfac = s.s_scale * m.irho;
+    d.acc[kDEk].add(0.5f * usq);
+    d.acc[kDEp].add(s.ep_scale * m.rho_p * m.rho_p);
+    d.acc[kDEpsK].add(s.epsk_scale * sfac * sfac * ss);
+    d.acc[kDDrho].add(m.drho);
+    d.acc[kDA].add(m.a);
+    d.acc[kDJx].add(m.jx);
+    d.acc[kDJy].add(m.jy);
+    d.acc[kDJz].add(m.jz);
+    d.umax = fmaxf(d.umax, sqrtf(usq));
+    if (s.fields) {
+        s.fields[idx] = m.rho_p;
+        s.fields[(size_t)n3 + idx] = m.ux;
+        s.fields[2 * (size_t)n3 + idx] = m.uy;
+        s.fields[3 * (size_t)n3 + idx] = m.uz;
+    }
+}
+
 struct StepArgs {
     void* f;          // QF * n3 elements, slot-major (f[i][z][y][x])
     void* g;          // QG * n3 elements
     Geometry geo;
     Phys ph;
+    DiagSink dg;      // used by the diagnosing variants only
 };
 
 // The fused AA update of one node: load the QF + QG populations (coalesced
 // along x), moments, coupled rho'/u solve, f and g collisions, store.
-template <class P, int FORCING, class T, bool ODD>
+// hook(h, m) runs between the moments and the collisions (the diagnosing
+// step kernels read the pre-collision state there).
+template <class P, int FORCING, class T, bool ODD, class Hook>
 __device__ __forceinline__ void update_node(void* fv, void* gv, const Geometry& geo, const Phys& ph, int x,
-                                            int y, int z)
+                                            int y, int z, Hook&& hook)
 {
     const NodeAddr a(geo, x, y, z);
     T* __restrict__ f = static_cast<T*>(fv);
@@ -27,10 +247,17 @@ __device__ __forceinline__ void update_node(void* fv, void* gv, const Geometry& 
     float h[P::QF], k[P::QG];
     load_node<typename P::LF, ODD, T>(f, n3, a, h);
     load_node<typename P::LG, ODD, T>(g, n3, a, k);
-    collide_node<P, FORCING, kExact>(h, k, ph);
+    collide_node<P, FORCING, kExact>(h, k, ph, hook);
     const NodeAddr b(geo, (int)launder(x), (int)launder(y), (int)launder(z));
     store_node<typename P::LF, ODD, T>(f, n3, b, h);
     store_node<typename P::LG, ODD, T>(g, n3, b, k);
+}
+
+template <class P, int FORCING, class T, bool ODD>
+__device__ __forceinline__ void update_node(void* fv, void* gv, const Geometry& geo, const Phys& ph, int x,
+                                            int y, int z)
+{
+    update_node<P, FORCING, T, ODD>(fv, gv, geo, ph, x, y, z, [](const float*, const Macro&) {});
 }
 
 // Three 256-thread blocks per SM (<= 85 registers): measured on the 256^3
@@ -48,6 +275,28 @@ __global__ void __launch_bounds__(256, LBM_STEP_MINBLOCKS) k_step(StepArgs args)
     const int z = blockIdx.z;
     if (x >= args.geo.nx || y >= args.geo.ny) return;
     update_node<P, FORCING, T, ODD>(args.f, args.g, args.geo, args.ph, x, y, z);
+}
+
+// The same step, also reducing the diagnostics (pass 1) of its input state,
+// the post-stream pre-collision populations of every node: one row of
+// partials per block (blocks numbered x fastest), FP32 fields for pass 2.
+template <class P, int FORCING, class T, bool ODD>
+__global__ void __launch_bounds__(256, 2) k_step_diag(StepArgs args)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    constexpr bool kExact = std::is_same<T, float>::value;
+    DiagAcc d;
+    if (x < args.geo.nx && y < args.geo.ny) {
+        const uint32_t idx = (uint32_t)x + (uint32_t)args.geo.nx * ((uint32_t)y + (uint32_t)args.geo.ny * (uint32_t)z);
+        update_node<P, FORCING, T, ODD>(args.f, args.g, args.geo, args.ph, x, y, z,
+                                        [&](const float* h, const Macro& m) {
+                                            diag_node<P, kExact>(h, m, args.dg, args.geo.n3, idx, d);
+                                        });
+    }
+    const uint32_t blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    d.store_block(args.dg.partials + (size_t)blk * kDNumSlots);
 }
 
 // ---------------------------------------------------------------------------
@@ -164,8 +413,10 @@ __device__ __forceinline__ void store_pair(unsigned short* __restrict__ b16, uin
 // Both nodes of a pair, in place on the packed words: the low-half node, then
 // the high-half node. Each result goes back into its half of the word before
 // the other node is unpacked, so only one node's values are live in FP32.
-template <class P, int FORCING, class T>
-__device__ __forceinline__ void collide_pair_words(uint32_t* wf, uint32_t* wg, const Phys& ph)
+// hook(which, h, m) sees node `which` (0 low, 1 high) between its moments
+// and its collisions.
+template <class P, int FORCING, class T, class Hook>
+__device__ __forceinline__ void collide_pair_words(uint32_t* wf, uint32_t* wg, const Phys& ph, Hook&& hook)
 {
     {
         float h[P::QF], k[P::QG];
@@ -173,7 +424,7 @@ __device__ __forceinline__ void collide_pair_words(uint32_t* wf, uint32_t* wg, c
         for (int i = 0; i < P::QF; ++i) h[i] = Pack16<T>::lo(wf[i]);
 #pragma unroll
         for (int i = 0; i < P::QG; ++i) k[i] = Pack16<T>::lo(wg[i]);
-        collide_node<P, FORCING, false>(h, k, ph);
+        collide_node<P, FORCING, false>(h, k, ph, [&](const float* hh, const Macro& m) { hook(0, hh, m); });
 #pragma unroll
         for (int i = 0; i < P::QF; ++i) wf[i] = __byte_perm(wf[i], Pack16<T>::bits(h[i]), 0x3254);
 #pragma unroll
@@ -185,12 +436,37 @@ __device__ __forceinline__ void collide_pair_words(uint32_t* wf, uint32_t* wg, c
         for (int i = 0; i < P::QF; ++i) h[i] = Pack16<T>::hi(wf[i]);
 #pragma unroll
         for (int i = 0; i < P::QG; ++i) k[i] = Pack16<T>::hi(wg[i]);
-        collide_node<P, FORCING, false>(h, k, ph);
+        collide_node<P, FORCING, false>(h, k, ph, [&](const float* hh, const Macro& m) { hook(1, hh, m); });
 #pragma unroll
         for (int i = 0; i < P::QF; ++i) wf[i] = __byte_perm(wf[i], Pack16<T>::bits(h[i]), 0x5410);
 #pragma unroll
         for (int i = 0; i < P::QG; ++i) wg[i] = __byte_perm(wg[i], Pack16<T>::bits(k[i]), 0x5410);
     }
+}
+
+template <class P, int FORCING, class T>
+__device__ __forceinline__ void collide_pair_words(uint32_t* wf, uint32_t* wg, const Phys& ph)
+{
+    collide_pair_words<P, FORCING, T>(wf, wg, ph, [](int, const float*, const Macro&) {});
+}
+
+// One pair's AA update: loads, both collisions, stores.
+template <class P, int FORCING, class T, bool ODD, class Hook>
+__device__ __forceinline__ void update_pair(const StepArgs& args, int x0, int y, int z, Hook&& hook)
+{
+    const uint32_t n3 = args.geo.n3;
+    unsigned short* fb = static_cast<unsigned short*>(args.f);
+    unsigned short* gb = static_cast<unsigned short*>(args.g);
+    uint32_t wf[P::QF], wg[P::QG];
+    {
+        const PairAddr a(args.geo, x0, y, z);
+        load_pair<typename P::LF, ODD>(fb, n3, a, wf);
+        load_pair<typename P::LG, ODD>(gb, n3, a, wg);
+    }
+    collide_pair_words<P, FORCING, T>(wf, wg, args.ph, hook);
+    const PairAddr b(args.geo, (int)launder(x0), (int)launder(y), (int)launder(z));
+    store_pair<typename P::LF, ODD>(fb, n3, b, wf);
+    store_pair<typename P::LG, ODD>(gb, n3, b, wg);
 }
 
 // Two 256-thread blocks per SM (<= 128 registers) for D3Q27xD3Q19, whose 46
@@ -206,19 +482,29 @@ __global__ void __launch_bounds__(256, kStep2MinBlocks<P>) k_step2(StepArgs args
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x0 >= args.geo.nx || y >= args.geo.ny) return;
-    const uint32_t n3 = args.geo.n3;
-    unsigned short* fb = static_cast<unsigned short*>(args.f);
-    unsigned short* gb = static_cast<unsigned short*>(args.g);
-    uint32_t wf[P::QF], wg[P::QG];
-    {
-        const PairAddr a(args.geo, x0, y, z);
-        load_pair<typename P::LF, ODD>(fb, n3, a, wf);
-        load_pair<typename P::LG, ODD>(gb, n3, a, wg);
+    update_pair<P, FORCING, T, ODD>(args, x0, y, z, [](int, const float*, const Macro&) {});
+}
+
+// k_step2 that also reduces the diagnostics (pass 1) of its input state, as
+// k_step_diag does.
+template <class P, int FORCING, class T, bool ODD>
+__global__ void __launch_bounds__(256, 2) k_step2_diag(StepArgs args)
+{
+    const int x0 = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    DiagAcc d;
+    if (x0 < args.geo.nx && y < args.geo.ny) {
+        const uint32_t row = (uint32_t)args.geo.nx * ((uint32_t)y + (uint32_t)args.geo.ny * (uint32_t)z);
+        // nodes of the pair: (x0, x0 + 1) even, (x0 - 1, x0) odd
+        const uint32_t lo = row + (uint32_t)(ODD ? (x0 == 0 ? args.geo.nx - 1 : x0 - 1) : x0);
+        const uint32_t hi = row + (uint32_t)(ODD ? x0 : x0 + 1);
+        update_pair<P, FORCING, T, ODD>(args, x0, y, z, [&](int which, const float* h, const Macro& m) {
+            diag_node<P, false>(h, m, args.dg, args.geo.n3, which ? hi : lo, d);
+        });
     }
-    collide_pair_words<P, FORCING, T>(wf, wg, args.ph);
-    const PairAddr b(args.geo, (int)launder(x0), (int)launder(y), (int)launder(z));
-    store_pair<typename P::LF, ODD>(fb, n3, b, wf);
-    store_pair<typename P::LG, ODD>(gb, n3, b, wg);
+    const uint32_t blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    d.store_block(args.dg.partials + (size_t)blk * kDNumSlots);
 }
 
 // Batched update: per-instance descriptor and launch arguments.
@@ -486,82 +772,13 @@ __global__ void k_set_pops(PopArgs a)
     }
 }
 
-// ---------------------------------------------------------------------------
-// Diagnostics (Eqs. 22-26), three deterministic passes.
-// ---------------------------------------------------------------------------
-enum DiagSlot : int {
-    kDEk = 0, kDEp, kDEpsK, kDDrho, kDA, kDJx, kDJy, kDJz, kDUmax,   // pass 1
-    kDEpsP, kDEpsKCurl,                                            // pass 2
-    kDNumSlots
-};
-constexpr int kDiagPass1 = 9;
-constexpr int kDiagPass2 = 2;
-constexpr int kDiagBlock = 256;
-
-struct DiagArgs {
-    const void* f;
-    const void* g;
-    Geometry geo;
-    Phys ph;
-    int odd;
-    float ep_scale;      // (G/N)^2 / (2 rho0^2)
-    float epsk_scale;    // 2 nu
-    float s_scale;       // -1 / (2 cs^2 tau_f)
-    float epsp_scale;    // D (G/N)^2 / rho0^2
-    float nu;
-    float* fields;       // 4 * n3: rho', ux, uy, uz (written by pass 1, read by pass 2)
-    double* partials;    // gridDim.x * kDNumSlots
-};
-
-// Compensated (Kahan) FP32 running sum for a thread's share of a diagnostics
-// reduction: within a few FP32 ulps of the exact sum of its terms, on the FP32
-// pipes (this GPU's FP64 rate is a small fraction of its FP32 rate). The
-// thread partials are then combined in FP64.
-struct KahanF {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float x)
-    {
-        const float y = x - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
-
-template <int NV, bool MAXLAST>
-__device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* out)
-{
-    __shared__ double sh[kDiagBlock / 32][NV];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            double t = __shfl_down_sync(0xffffffffu, v[q], o);
-            v[q] = (MAXLAST && q == NV - 1) ? fmax(v[q], t) : v[q] + t;
-        }
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int q = 0; q < NV; ++q) sh[wid][q] = v[q];
-    }
-    __syncthreads();
-    if (threadIdx.x < NV) {
-        const int q = threadIdx.x;
-        double acc = sh[0][q];
-        for (int w = 1; w < kDiagBlock / 32; ++w) acc = (MAXLAST && q == NV - 1) ? fmax(acc, sh[w][q]) : acc + sh[w][q];
-        out[q] = acc;
-    }
-}
-
 template <class P, class T>
 __global__ void __launch_bounds__(kDiagBlock) k_diag_moments(DiagArgs a)
 {
     using LF = typename P::LF;
     const uint32_t n3 = a.geo.n3;
-    KahanF acc[kDiagPass1 - 1];
-    float umax = 0.f;
+    const DiagSink sink{a.ep_scale, a.epsk_scale, a.s_scale, a.fields, a.partials};
+    DiagAcc d;
     for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n3; idx += gridDim.x * blockDim.x) {
         int x, y, z;
         node_xyz(a.geo, idx, x, y, z);
@@ -575,64 +792,9 @@ __global__ void __launch_bounds__(kDiagBlock) k_diag_moments(DiagArgs a)
             load_node<typename P::LG, false, T>(static_cast<const T*>(a.g), n3, na, k);
         }
         const Macro m = node_macro<P>(h, k, a.ph);
-        // second moment of the deviations: M2 = sum e e h; Pi_neq = M2 - rho u u - drho cs^2 I.
-        // node_macro left each opposite pair as (sum, difference); e e is the same
-        // for e and -e, so a pair contributes e e (h_i + h_j), its stored sum.
-        // D3Q7 lacks the fourth-order isotropy behind sum e e f_eq = rho u u +
-        // rho cs^2 I, so there the pair sums of f_eq(rho, u) are subtracted
-        // explicitly and the closed-form terms below are not.
-        constexpr bool kExplicit = (LF::kQ == 7);
-        const float usq = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
-        float mxx = 0.f, myy = 0.f, mzz = 0.f, mxy = 0.f, mxz = 0.f, myz = 0.f;
-        sfor<0, kPairs<LF>>([&](auto mc) {
-            constexpr int i = 2 * decltype(mc)::value + 1;
-            float sp = h[i];
-            if constexpr (kExplicit) {
-                const float eu = e_dot<LF, i>(m.ux, m.uy, m.uz);
-                sp -= 2.f * LF::w(i) * (m.drho + m.rho * (LF::half_inv_cs4 * eu * eu - LF::half_inv_cs2 * usq));
-            }
-            if constexpr (LF::ex(i) != 0) mxx += sp;
-            if constexpr (LF::ey(i) != 0) myy += sp;
-            if constexpr (LF::ez(i) != 0) mzz += sp;
-            if constexpr (LF::ex(i) * LF::ey(i) == 1) mxy += sp;
-            if constexpr (LF::ex(i) * LF::ey(i) == -1) mxy -= sp;
-            if constexpr (LF::ex(i) * LF::ez(i) == 1) mxz += sp;
-            if constexpr (LF::ex(i) * LF::ez(i) == -1) mxz -= sp;
-            if constexpr (LF::ey(i) * LF::ez(i) == 1) myz += sp;
-            if constexpr (LF::ey(i) * LF::ez(i) == -1) myz -= sp;
-        });
-        const float dc = kExplicit ? 0.f : m.drho * LF::cs2;
-        const float rr = kExplicit ? 0.f : m.rho;
-        // S = s_scale / rho * (Pi_neq + (u F + F u) / 2), F = (0, 0, Fz)
-        const float pxx = mxx - rr * m.ux * m.ux - dc;
-        const float pyy = myy - rr * m.uy * m.uy - dc;
-        const float pzz = mzz - rr * m.uz * m.uz - dc + m.uz * m.Fz;
-        const float pxy = mxy - rr * m.ux * m.uy;
-        const float pxz = mxz - rr * m.ux * m.uz + 0.5f * m.ux * m.Fz;
-        const float pyz = myz - rr * m.uy * m.uz + 0.5f * m.uy * m.Fz;
-        const float ss = pxx * pxx + pyy * pyy + pzz * pzz + 2.f * (pxy * pxy + pxz * pxz + pyz * pyz);
-        const float sfac = a.s_scale * m.irho;
-        acc[kDEk].add(0.5f * usq);
-        acc[kDEp].add(a.ep_scale * m.rho_p * m.rho_p);
-        acc[kDEpsK].add(a.epsk_scale * sfac * sfac * ss);
-        acc[kDDrho].add(m.drho);
-        acc[kDA].add(m.a);
-        acc[kDJx].add(m.jx);
-        acc[kDJy].add(m.jy);
-        acc[kDJz].add(m.jz);
-        umax = fmaxf(umax, sqrtf(usq));
-        if (a.fields) {
-            a.fields[idx] = m.rho_p;
-            a.fields[(size_t)n3 + idx] = m.ux;
-            a.fields[2 * (size_t)n3 + idx] = m.uy;
-            a.fields[3 * (size_t)n3 + idx] = m.uz;
-        }
+        diag_node<P, true>(h, m, sink, n3, idx, d);
     }
-    double v[kDiagPass1];
-#pragma unroll
-    for (int q = 0; q < kDiagPass1 - 1; ++q) v[q] = acc[q].value();
-    v[kDUmax] = (double)umax;
-    block_reduce_store<kDiagPass1, true>(v, a.partials + (size_t)blockIdx.x * kDNumSlots);
+    d.store_block(a.partials + (size_t)blockIdx.x * kDNumSlots);
 }
 
 #ifdef LBM_REDUCTION_KERNELS  // defined in exactly one translation unit
@@ -666,22 +828,102 @@ __global__ void __launch_bounds__(kDiagBlock) k_diag_gradients(DiagArgs a)
 }
 
 // Final pass: one block adds the per-block partials in a fixed order.
-__global__ void __launch_bounds__(kDiagBlock) k_diag_final(const double* partials, int nblocks, double* out)
+// Block b of the grid sums its share of the rows: pass-1 slots from the first
+// nb1 rows, pass-2 slots from the first nb2, split into gridDim.x contiguous
+// ranges in order. The pass-1 slots hold FP32 (hi, lo) pairs (DiagAcc; the
+// diagnosing step kernels write one row per step block, 65536 rows at
+// 256^3), summed with two-sum on the FP32 pipes; the pass-2 slots FP64
+// values. With one block the totals go to out[0..kDNumSlots) as FP64; with
+// more (a first level that spreads the row reads over the SMs) each block
+// writes its row of out in the input's format.
+__global__ void __launch_bounds__(kDiagBlock) k_diag_final(const double* partials, int nb1, int nb2, double* out)
 {
+    constexpr bool pass1_pairs = true;
+    const int per1 = (nb1 + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int per2 = (nb2 + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int b1 = (int)blockIdx.x * per1, e1 = min(nb1, b1 + per1);
+    const int b2 = (int)blockIdx.x * per2, e2 = min(nb2, b2 + per2);
+    const bool pairs_out = pass1_pairs && gridDim.x > 1;
     double acc[kDNumSlots];
 #pragma unroll
     for (int q = 0; q < kDNumSlots; ++q) acc[q] = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    float hi[kDiagPass1], lo[kDiagPass1];
 #pragma unroll
-        for (int q = 0; q < kDNumSlots; ++q) {
-            const double v = partials[(size_t)b * kDNumSlots + q];
-            acc[q] = (q == kDUmax) ? fmax(acc[q], v) : acc[q] + v;
+    for (int q = 0; q < kDiagPass1; ++q) hi[q] = lo[q] = 0.f;
+    {
+        for (int b = b1 + (int)threadIdx.x; b < e1; b += blockDim.x) {
+            const float2* row = reinterpret_cast<const float2*>(partials + (size_t)b * kDNumSlots);
+#pragma unroll
+            for (int q = 0; q < kDiagPass1; ++q) {
+                const float2 v = row[q];
+                if (q == kDUmax) {
+                    hi[q] = fmaxf(hi[q], v.x);
+                } else {
+                    float t, e;
+                    two_sum(hi[q], v.x, t, e);
+                    hi[q] = t;
+                    lo[q] = lo[q] + v.y + e;
+                }
+            }
+        }
+        if (!pairs_out) {
+#pragma unroll
+            for (int q = 0; q < kDiagPass1; ++q) acc[q] = (double)hi[q] + (double)lo[q];
+        }
+    }
+    for (int b = b2 + (int)threadIdx.x; b < e2; b += blockDim.x) {
+#pragma unroll
+        for (int q = kDiagPass1; q < kDNumSlots; ++q) acc[q] += partials[(size_t)b * kDNumSlots + q];
+    }
+    double* dst = out + (size_t)blockIdx.x * kDNumSlots;
+    if (pairs_out) {
+        // pass-1 pairs through the block in FP32 two-sum, pass-2 in FP64 below
+        __shared__ float shp[kDiagBlock / 32][kDiagPass1][2];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int q = 0; q < kDiagPass1; ++q) {
+                const float oh = __shfl_down_sync(0xffffffffu, hi[q], o);
+                const float ol = __shfl_down_sync(0xffffffffu, lo[q], o);
+                if (q == kDUmax) {
+                    hi[q] = fmaxf(hi[q], oh);
+                } else {
+                    float t, e;
+                    two_sum(hi[q], oh, t, e);
+                    hi[q] = t;
+                    lo[q] = lo[q] + ol + e;
+                }
+            }
+        }
+        if (lane == 0)
+            for (int q = 0; q < kDiagPass1; ++q) {
+                shp[wid][q][0] = hi[q];
+                shp[wid][q][1] = lo[q];
+            }
+        __syncthreads();
+        if (threadIdx.x < kDiagPass1) {
+            const int q = threadIdx.x;
+            float h = shp[0][q][0], l = shp[0][q][1];
+            for (int w = 1; w < kDiagBlock / 32; ++w) {
+                if (q == kDUmax) {
+                    h = fmaxf(h, shp[w][q][0]);
+                } else {
+                    float t, e;
+                    two_sum(h, shp[w][q][0], t, e);
+                    h = t;
+                    l = l + shp[w][q][1] + e;
+                }
+            }
+            reinterpret_cast<float2*>(dst)[q] = make_float2(h, l);
         }
     }
     __shared__ double sh[kDiagBlock / 32][kDNumSlots];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int q0 = pairs_out ? kDiagPass1 : 0;   // slots reduced in FP64 here
 #pragma unroll
     for (int q = 0; q < kDNumSlots; ++q) {
+        if (q < q0) continue;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const double t = __shfl_down_sync(0xffffffffu, acc[q], o);
@@ -689,13 +931,13 @@ __global__ void __launch_bounds__(kDiagBlock) k_diag_final(const double* partial
         }
     }
     if (lane == 0)
-        for (int q = 0; q < kDNumSlots; ++q) sh[wid][q] = acc[q];
+        for (int q = q0; q < kDNumSlots; ++q) sh[wid][q] = acc[q];
     __syncthreads();
-    if (threadIdx.x < kDNumSlots) {
+    if ((int)threadIdx.x >= q0 && threadIdx.x < kDNumSlots) {
         const int q = threadIdx.x;
         double v = sh[0][q];
         for (int w = 1; w < kDiagBlock / 32; ++w) v = (q == kDUmax) ? fmax(v, sh[w][q]) : v + sh[w][q];
-        out[q] = v;
+        dst[q] = v;
     }
 }
 

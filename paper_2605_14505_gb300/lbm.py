@@ -92,6 +92,7 @@ _SIGS = {
     "lbm_step": ([_H, ctypes.c_int64], ctypes.c_int),
     "lbm_synchronize": ([_H], ctypes.c_int),
     "lbm_diagnostics": ([_H, ctypes.POINTER(lbm_diag)], ctypes.c_int),
+    "lbm_step_diagnostics": ([_H, ctypes.c_int64, ctypes.POINTER(lbm_diag)], ctypes.c_int),
     "lbm_diagnostics_noalloc": ([_H, ctypes.POINTER(lbm_diag)], ctypes.c_int),
     "lbm_get_fields": ([_H, _DP, _DP, _DP], ctypes.c_int),
     "lbm_get_populations": ([_H, _DP, _DP], ctypes.c_int),
@@ -261,6 +262,16 @@ def lbm_diagnostics(h, allow_nonfinite: bool = False) -> dict:
     return d.as_dict()
 
 
+def lbm_step_diagnostics(h, nsteps: int, allow_nonfinite: bool = False) -> dict:
+    """Diagnostics of the current state, reduced inside the first of `nsteps`
+    steps, which then all run."""
+    d = lbm_diag()
+    rc = load_library().lbm_step_diagnostics(h, int(nsteps), ctypes.byref(d))
+    if not (allow_nonfinite and rc == -5):
+        _check(rc)
+    return d.as_dict()
+
+
 def lbm_diagnostics_noalloc(h) -> dict:
     """lbm_diagnostics without any device allocation (eps_p, eps_k_curl are NaN)."""
     d = lbm_diag()
@@ -411,6 +422,9 @@ class Simulation:
 
     def diagnostics(self, allow_nonfinite=False) -> dict:
         return lbm_diagnostics(self.h, allow_nonfinite)
+
+    def step_diagnostics(self, n, allow_nonfinite=False) -> dict:
+        return lbm_step_diagnostics(self.h, n, allow_nonfinite)
 
     def fields(self):
         return lbm_get_fields(self.h, self.n3)

@@ -357,3 +357,42 @@ def test_16bit_odd_nx_one_node_kernel_against_oracle(storage, shape):
         df, dg = fo - wf[:, None], go - p.rho0 * wg[:, None]
         assert np.max(np.abs(fg - fo)) <= 4 * ulp * np.max(np.abs(df)) + 2.0 ** -23
         assert np.max(np.abs(gg - go)) <= 4 * ulp * np.max(np.abs(dg)) + 2.0 ** -23
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("pair", ["27x19", "19x7"])
+def test_fused_step_diagnostics_match_separate_calls(storage, pair):
+    """lbm_step_diagnostics (diagnostics reduced inside the first step) equals
+    lbm_diagnostics followed by lbm_step on the same state. FP32 storage: the
+    same FP32 node values summed per step-kernel block instead of per
+    diagnostics block, so within 1e-9 relative; 16-bit storage: the node
+    moments come from the step's short-form FP32 arithmetic, so within 1e-6
+    (momentum, which cancels, 1e-6 absolute). The state afterwards is within
+    FP32 rounding of the plain steps, at both AA parities."""
+    n = 40
+    p = lbm.lbm_params_from_physics(n, n, n, pair, "sc", 200.0, 0.2, 1.0, 0.04)
+    a = gpu_sim(p, storage)
+    b = gpu_sim(p, storage)
+    for s in (a, b):
+        s.init_tgv(seed=5, noise_amp=0.01)
+        s.step(3)   # odd layout
+    for chunk in (7, 12):
+        da = a.step_diagnostics(chunk)
+        db = b.diagnostics()
+        b.step(chunk)
+        assert da["step"] == db["step"]
+        rel = 1e-9 if storage == "fp32" else 1e-6
+        for key in ("Ek", "Ep", "eps_k", "eps_p", "eps_k_curl", "mass_f", "mass_g", "umax"):
+            assert abs(da[key] - db[key]) <= rel * abs(db[key]) + 1e-15, (key, da[key], db[key])
+        for key in ("mom_x", "mom_y", "mom_z"):
+            assert abs(da[key] - db[key]) <= 1e-6, (key, da[key], db[key])
+        a.synchronize()
+        fa, ga = a.populations()
+        fb, gb = b.populations()
+        qf, _ = lbm.PAIR_Q[p.pair]
+        _, wf, _ = lbm.lbm_velocity_set(qf)
+        tol = 1e-6 if storage == "fp32" else 2.0 ** -9
+        assert np.all(np.abs(fa - fb) <= tol * np.max(np.abs(fb - wf[:, None])) + 1e-12)
+        assert np.all(np.abs(ga - gb) <= tol * np.max(np.abs(gb)) + 1e-12)
+    with pytest.raises(lbm.LbmError):
+        a.step_diagnostics(0)
