@@ -174,15 +174,34 @@ int lbm_init_tgv(lbm_handle h, uint64_t seed, double noise_amp);
  * rho_p[n3]; f = f_eq(rho, u) + amp w_i xi_f[code(e_i)][node],
  * g = g_eq(rho', u) + amp w_i xi_g[code(e_i)][node], where the optional
  * xi_f, xi_g are [27][n3] arrays indexed by code(e) = (ex+1)*9 + (ey+1)*3 +
- * (ez+1) (NULL: no perturbation). Waits for completion. Resets the step counter. */
+ * (ez+1) (NULL: no perturbation). Returns once the host arrays have been
+ * copied (they may then be reused); the initialisation completes in order on
+ * the handle's stream. Resets the step counter. */
 int lbm_init_fields(lbm_handle h, const double* rho, const double* u, const double* rho_p,
                     const double* xi_f, const double* xi_g, double amp);
+
+/* Pipelined initialisation from host fields, for callers that start a new
+ * state every few steps (ensembles, restarts from host data): the
+ * host-to-device copies of the next state's fields overlap the current
+ * steps. lbm_prefetch_fields enqueues the copies of rho[n3], u[3*n3],
+ * rho_p[n3] (host FP64, pinned for the overlap) into one of two library
+ * buffers on an internal copy stream and returns at once; the arrays must
+ * stay unchanged until the matching lbm_init_prefetched (or lbm_synchronize)
+ * returns. lbm_init_prefetched sets the populations from the last prefetch
+ * as lbm_init_fields does without perturbation (f = f_eq(rho, u),
+ * g = g_eq(rho', u)), in order on the handle's stream after the copies, and
+ * resets the step counter. Errors: LBM_ESTATE for a second prefetch before
+ * its init, or an init without a prefetch; LBM_ENOMEM if the two buffers
+ * (10 * n3 doubles) cannot be allocated on the first prefetch. */
+int lbm_prefetch_fields(lbm_handle h, const double* rho, const double* u, const double* rho_p);
+int lbm_init_prefetched(lbm_handle h);
 
 /* Advance nsteps >= 0 time steps (Eqs. 5, 11: collide, then stream) with
  * the in-place AA pattern; asynchronous on the handle's stream. */
 int lbm_step(lbm_handle h, int64_t nsteps);
 
-/* Block until the handle's stream is idle; reports asynchronous CUDA errors. */
+/* Block until the handle's stream (and its prefetch copies) are idle;
+ * reports asynchronous CUDA errors. */
 int lbm_synchronize(lbm_handle h);
 
 /* Diagnostics of the current state into *out (waits for the stream).

@@ -100,6 +100,16 @@ struct lbm_ctx {
     // host<->device staging
     double* staging = nullptr;
     size_t staging_bytes = 0;
+    cudaEvent_t copy_event = nullptr;   // host->device copies of lbm_init_fields done
+    // lbm_prefetch_fields / lbm_init_prefetched: two device buffers of the
+    // five FP64 fields, filled on a copy stream while the lattice steps
+    double* pre[2] = {nullptr, nullptr};
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t pre_done[2] = {nullptr, nullptr};   // copies into pre[b] complete
+    cudaEvent_t pre_free[2] = {nullptr, nullptr};   // the init that read pre[b] complete
+    bool pre_free_recorded[2] = {false, false};
+    int pre_next = 0;     // buffer the next prefetch fills
+    int pre_ready = -1;   // buffer holding a prefetch not yet used, or -1
     // CUDA graph of kGraphSteps steps starting from the natural layout
     bool graphs = true;
     cudaGraphExec_t graph = nullptr;
@@ -195,6 +205,10 @@ void* g_ptr(lbm_ctx* h)
 
 int ensure_staging(lbm_ctx* h, size_t bytes)
 {
+    if (!h->copy_event && cudaEventCreateWithFlags(&h->copy_event, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ECUDA, "event creation failed");
+    }
     if (h->staging_bytes >= bytes) return LBM_OK;
     if (h->staging) cudaFree(h->staging);
     h->staging = nullptr;
@@ -565,17 +579,30 @@ int lbm_init_tgv(lbm_handle h, uint64_t seed, double noise_amp)
     if (h->p.nx != h->p.ny || h->p.nx != h->p.nz) return fail(LBM_EINVAL, "the Taylor-Green box needs nx = ny = nz");
     if (!std::isfinite(noise_amp)) return fail(LBM_EINVAL, "non-finite noise amplitude");
     if ((rc = ensure_store(h))) return rc;
-    drop_graph(h);
+    // sin and cos of x_i = 2 pi i / n for the kernel, in the staging buffer
+    const int n = h->p.nx;
+    std::vector<double> trig(2 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const double x = 6.283185307179586476925286766559 * i / n;
+        trig[i] = std::sin(x);
+        trig[n + i] = std::cos(x);
+    }
+    if ((rc = ensure_staging(h, trig.size() * sizeof(double)))) return rc;
+    LBM_CUDA(cudaMemcpyAsync(h->staging, trig.data(), trig.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream),
+             "copy trig table");
+    LBM_CUDA(cudaEventRecord(h->copy_event, h->stream), "init_tgv event");
     TgvArgs a;
     a.f = f_ptr(h);
     a.g = g_ptr(h);
     a.geo = h->geo;
+    a.trig = h->staging;
     a.U0 = h->p.U0;
     a.noise = noise_amp;
     a.seed = seed;
     a.rho0 = h->p.rho0;
     void* args[] = {&a};
     LBM_CUDA(cudaLaunchKernel(h->ks->init_tgv, dim3(flat_grid(h)), dim3(256), args, 0, h->stream), "init_tgv launch");
+    LBM_CUDA(cudaEventSynchronize(h->copy_event), "init_tgv");   // the table's host copy may go
     return after_init(h);
 }
 
@@ -589,7 +616,6 @@ int lbm_init_fields(lbm_handle h, const double* rho, const double* u, const doub
     const size_t n3 = h->geo.n3;
     size_t ndoubles = 5 * n3 + (xi_f ? 27 * n3 : 0) + (xi_g ? 27 * n3 : 0);
     if ((rc = ensure_staging(h, ndoubles * sizeof(double)))) return rc;
-    drop_graph(h);
     double* d = h->staging;
     LBM_CUDA(cudaMemcpyAsync(d, rho, n3 * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy rho");
     LBM_CUDA(cudaMemcpyAsync(d + n3, u, 3 * n3 * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy u");
@@ -615,12 +641,78 @@ int lbm_init_fields(lbm_handle h, const double* rho, const double* u, const doub
     a.rho_p = d + 4 * n3;
     a.xi_f = dxf;
     a.xi_g = dxg;
-    a.amp = amp;
+    a.amp_f = (float)amp;
+    a.rho0 = h->p.rho0;
+    void* args[] = {&a};
+    // the host arrays may be reused once the copies are done; the
+    // initialisation itself completes in stream order
+    LBM_CUDA(cudaEventRecord(h->copy_event, h->stream), "init_fields event");
+    LBM_CUDA(cudaLaunchKernel(h->ks->init_fields, dim3(flat_grid(h)), dim3(256), args, 0, h->stream),
+             "init_fields launch");
+    LBM_CUDA(cudaEventSynchronize(h->copy_event), "init_fields");
+    return after_init(h);
+}
+
+int lbm_prefetch_fields(lbm_handle h, const double* rho, const double* u, const double* rho_p)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!rho || !u || !rho_p) return fail(LBM_EINVAL, "rho, u and rho_p are required");
+    if (h->pre_ready >= 0) return fail(LBM_ESTATE, "a prefetch is already waiting for lbm_init_prefetched");
+    const size_t n3 = h->geo.n3;
+    if (!h->copy_stream) {
+        if (cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LBM_ECUDA, "copy stream creation failed");
+        }
+        for (int b = 0; b < 2; ++b) {
+            if (cudaEventCreateWithFlags(&h->pre_done[b], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->pre_free[b], cudaEventDisableTiming) != cudaSuccess ||
+                cudaMalloc(&h->pre[b], 5 * n3 * sizeof(double)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(LBM_ENOMEM, "prefetch buffer allocation failed");
+            }
+        }
+    }
+    const int b = h->pre_next;
+    if (h->pre_free_recorded[b])
+        LBM_CUDA(cudaStreamWaitEvent(h->copy_stream, h->pre_free[b], 0), "prefetch wait");
+    double* d = h->pre[b];
+    LBM_CUDA(cudaMemcpyAsync(d, rho, n3 * sizeof(double), cudaMemcpyHostToDevice, h->copy_stream), "prefetch rho");
+    LBM_CUDA(cudaMemcpyAsync(d + n3, u, 3 * n3 * sizeof(double), cudaMemcpyHostToDevice, h->copy_stream), "prefetch u");
+    LBM_CUDA(cudaMemcpyAsync(d + 4 * n3, rho_p, n3 * sizeof(double), cudaMemcpyHostToDevice, h->copy_stream),
+             "prefetch rho_p");
+    LBM_CUDA(cudaEventRecord(h->pre_done[b], h->copy_stream), "prefetch event");
+    h->pre_ready = b;
+    h->pre_next = b ^ 1;
+    return LBM_OK;
+}
+
+int lbm_init_prefetched(lbm_handle h)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (h->pre_ready < 0) return fail(LBM_ESTATE, "lbm_init_prefetched without a prefetch");
+    if ((rc = ensure_store(h))) return rc;
+    const int b = h->pre_ready;
+    const size_t n3 = h->geo.n3;
+    LBM_CUDA(cudaStreamWaitEvent(h->stream, h->pre_done[b], 0), "init wait");
+    InitArgs a{};
+    a.f = f_ptr(h);
+    a.g = g_ptr(h);
+    a.geo = h->geo;
+    a.rho = h->pre[b];
+    a.u = h->pre[b] + n3;
+    a.rho_p = h->pre[b] + 4 * n3;
     a.rho0 = h->p.rho0;
     void* args[] = {&a};
     LBM_CUDA(cudaLaunchKernel(h->ks->init_fields, dim3(flat_grid(h)), dim3(256), args, 0, h->stream),
-             "init_fields launch");
-    LBM_CUDA(cudaStreamSynchronize(h->stream), "init_fields");
+             "init_prefetched launch");
+    LBM_CUDA(cudaEventRecord(h->pre_free[b], h->stream), "init event");
+    h->pre_free_recorded[b] = true;
+    h->pre_ready = -1;
+    // the caller's host arrays of this prefetch may be reused from here on
+    LBM_CUDA(cudaEventSynchronize(h->pre_done[b]), "prefetch copies");
     return after_init(h);
 }
 
@@ -667,6 +759,7 @@ int lbm_synchronize(lbm_handle h)
     int rc = check_handle(h);
     if (rc) return rc;
     LBM_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    if (h->copy_stream) LBM_CUDA(cudaStreamSynchronize(h->copy_stream), "copy stream synchronize");
     int err = 0;
     LBM_CUDA(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag read");
     if (err) {
@@ -1114,6 +1207,14 @@ int lbm_destroy(lbm_handle h)
     if (h->diag_out) cudaFree(h->diag_out);
     if (h->diag_host) cudaFreeHost(h->diag_host);
     if (h->diag_event) cudaEventDestroy(h->diag_event);
+    if (h->copy_event) cudaEventDestroy(h->copy_event);
+    if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
+    for (int b = 0; b < 2; ++b) {
+        if (h->pre[b]) cudaFree(h->pre[b]);
+        if (h->pre_done[b]) cudaEventDestroy(h->pre_done[b]);
+        if (h->pre_free[b]) cudaEventDestroy(h->pre_free[b]);
+    }
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     if (h->d_err) cudaFree(h->d_err);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;

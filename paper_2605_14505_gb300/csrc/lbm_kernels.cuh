@@ -552,7 +552,7 @@ struct InitArgs {
     const double* rho_p;
     const double* xi_f;
     const double* xi_g;
-    double amp;
+    float amp_f;      // perturbation amplitude (the perturbation is arithmetic in FP32)
     double rho0;
 };
 
@@ -597,13 +597,13 @@ __global__ void k_init_fields(InitArgs a)
         sfor<0, P::QF>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             float v = hf[i];
-            if (a.xi_f) v += (float)(a.amp * LF::wd(i) * a.xi_f[(size_t)canon_code<LF>(i) * n3 + idx]);
+            if (a.xi_f) v += a.amp_f * LF::w(i) * (float)a.xi_f[(size_t)canon_code<LF>(i) * n3 + idx];
             st_pop<T>(f + (size_t)i * n3 + idx, v);
         });
         sfor<0, P::QG>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             float v = hg[i];
-            if (a.xi_g) v += (float)(a.amp * LG::wd(i) * a.xi_g[(size_t)canon_code<LG>(i) * n3 + idx]);
+            if (a.xi_g) v += a.amp_f * LG::w(i) * (float)a.xi_g[(size_t)canon_code<LG>(i) * n3 + idx];
             st_pop<T>(g + (size_t)i * n3 + idx, v);
         });
     }
@@ -624,6 +624,7 @@ struct TgvArgs {
     void* f;
     void* g;
     Geometry geo;
+    const double* trig;   // sin(2 pi i / n), cos(2 pi i / n), i < n (n = nx = ny = nz)
     double U0;
     double noise;     // noise amplitude relative to U0 (0: pure Eq. 20)
     uint64_t seed;
@@ -637,14 +638,15 @@ __global__ void k_init_tgv(TgvArgs a)
     using LF = typename P::LF;
     using LG = typename P::LG;
     const uint32_t n3 = a.geo.n3;
-    const double two_pi = 6.283185307179586476925286766559;
-    const double dx = two_pi / a.geo.nx, dy = two_pi / a.geo.ny, dz = two_pi / a.geo.nz;
+    // the factors of Eq. 20 depend on one coordinate each: tabulated once
+    // (FP64, by the host) instead of five FP64 trigonometric calls per node
+    const double* sn = a.trig;
+    const double* cs = a.trig + a.geo.nx;
     for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n3; idx += gridDim.x * blockDim.x) {
         int x, y, z;
         node_xyz(a.geo, idx, x, y, z);
-        const double X = x * dx, Y = y * dy, Z = z * dz;
-        double ux = a.U0 * sin(X) * cos(Y) * cos(Z);
-        double uy = -a.U0 * cos(X) * sin(Y) * cos(Z);
+        double ux = a.U0 * sn[x] * cs[y] * cs[z];
+        double uy = -a.U0 * cs[x] * sn[y] * cs[z];
         double uz = 0.0;
         if (a.noise != 0.0) {
             ux += a.noise * a.U0 * uniform_pm1(a.seed, idx);

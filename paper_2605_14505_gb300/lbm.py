@@ -93,6 +93,8 @@ _SIGS = {
     "lbm_synchronize": ([_H], ctypes.c_int),
     "lbm_diagnostics": ([_H, ctypes.POINTER(lbm_diag)], ctypes.c_int),
     "lbm_step_diagnostics": ([_H, ctypes.c_int64, ctypes.POINTER(lbm_diag)], ctypes.c_int),
+    "lbm_prefetch_fields": ([_H, _DP, _DP, _DP], ctypes.c_int),
+    "lbm_init_prefetched": ([_H], ctypes.c_int),
     "lbm_diagnostics_noalloc": ([_H, ctypes.POINTER(lbm_diag)], ctypes.c_int),
     "lbm_get_fields": ([_H, _DP, _DP, _DP], ctypes.c_int),
     "lbm_get_populations": ([_H, _DP, _DP], ctypes.c_int),
@@ -244,6 +246,29 @@ def lbm_init_fields(h, rho, u, rho_p, xi_f=None, xi_g=None, amp: float = 0.0):
     xi_f = None if xi_f is None else _f64(xi_f)
     xi_g = None if xi_g is None else _f64(xi_g)
     _check(load_library().lbm_init_fields(h, _dp(rho), _dp(u), _dp(rho_p), _dp(xi_f), _dp(xi_g), amp))
+
+
+def _host_f64_ptr(x):
+    """Pointer to a C-contiguous float64 host array (numpy, or a CPU torch
+    tensor, e.g. in pinned memory) without copying it."""
+    if hasattr(x, "data_ptr"):
+        if x.dtype.__str__() != "torch.float64" or x.is_cuda or not x.is_contiguous():
+            raise ValueError("expected a contiguous CPU float64 tensor")
+        return ctypes.cast(x.data_ptr(), _DP)
+    if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous):
+        raise ValueError("expected a C-contiguous float64 array")
+    return x.ctypes.data_as(_DP)
+
+
+def lbm_prefetch_fields(h, rho, u, rho_p):
+    """Start the host-to-device copies of the next state's fields (see the C
+    header); the arrays must stay alive and unchanged until
+    lbm_init_prefetched returns."""
+    _check(load_library().lbm_prefetch_fields(h, _host_f64_ptr(rho), _host_f64_ptr(u), _host_f64_ptr(rho_p)))
+
+
+def lbm_init_prefetched(h):
+    _check(load_library().lbm_init_prefetched(h))
 
 
 def lbm_step(h, nsteps: int):

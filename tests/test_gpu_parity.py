@@ -396,3 +396,32 @@ def test_fused_step_diagnostics_match_separate_calls(storage, pair):
         assert np.all(np.abs(ga - gb) <= tol * np.max(np.abs(gb)) + 1e-12)
     with pytest.raises(lbm.LbmError):
         a.step_diagnostics(0)
+
+
+def test_prefetched_initialisation_matches_init_fields():
+    """lbm_prefetch_fields + lbm_init_prefetched (copies on a side stream,
+    overlapping the running steps, two alternating buffers) give the same
+    populations as lbm_init_fields, bit for bit, over three rounds; misuse is
+    reported."""
+    n = 24
+    p = lbm.lbm_params_from_physics(n, n, n, "27x19", "sc", 100.0, 0.5, 1.0, 0.04)
+    a = gpu_sim(p)
+    b = gpu_sim(p)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_init_prefetched(a.h)
+    fields = [I.tgv_fields(n, 0.04, seed=s, noise_amp=0.05) for s in (1, 2, 3)]
+    lbm.lbm_prefetch_fields(a.h, *fields[0])
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_prefetch_fields(a.h, *fields[0])
+    for k in range(3):
+        lbm.lbm_init_prefetched(a.h)
+        if k + 1 < 3:
+            lbm.lbm_prefetch_fields(a.h, *fields[k + 1])
+        a.step(5)
+        b.init_fields(*fields[k])
+        b.step(5)
+        a.synchronize()
+        fa, ga = a.populations()
+        fb, gb = b.populations()
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb), k
+        assert a.step_count == 5
