@@ -132,6 +132,7 @@ void derive_phys(lbm_ctx* h)
     ph.kappa = (float)(c_mom * -p.beta);
     ph.c_lbe = (float)c_lbe;
     ph.guo_pref = (float)(1.0 - 1.0 / (2.0 * p.tau_f));
+    ph.guo_tau = (float)(p.tau_f - 0.5);
     ph.sc_tau = (float)(p.sc_shift * p.tau_f);
     h->geo.nx = p.nx;
     h->geo.ny = p.ny;

@@ -163,6 +163,7 @@ struct Phys {
     float c_lbe;      // factor of S_i in the g update (Eq. 11)
     float guo_pref;   // 1 - 1 / (2 tau_f)
     float sc_tau;     // shift * tau_f of the Shan-Chen equilibrium velocity (Eq. 10)
+    float guo_tau;    // tau_f - 1/2 = (1 - 1 / (2 tau_f)) tau_f: the Guo source over 1 / tau_f
 };
 
 struct Geometry {
@@ -417,17 +418,28 @@ LBM_HD void collide_f(float* h, const Macro& m, const Phys& ph)
     }
     const float vx = fmaf(mx, m.dirho, mx), vy = fmaf(my, m.dirho, my), vz = fmaf(mz, m.dirho, mz);
     const float vsq = vx * vx + vy * vy + vz * vz;
-    const float base = m.drho - c0 * (mx * vx + my * vy + mz * vz);
+    float base = m.drho - c0 * (mx * vx + my * vy + mz * vz);
+    // Guo: the source is linear in F, so it folds into the equilibrium that
+    // the relaxation weights by 1/tau: S_i tau = (tau - 1/2) w [(e - v)/cs^2 +
+    // (e.v) e / cs^4] . F adds (tau - 1/2) F_z to the momentum of the odd part
+    // (mzo), 2 (tau - 1/2) F_z to the e.(rho v) factor of the even part (mze)
+    // and -(tau - 1/2) F_z v_z / cs^2 to its base. Other schemes: mzo = mze = mz.
+    float mze = mz, mzo = mz;
+    if constexpr (FORCING == kGuo) {
+        const float gFo = ph.guo_tau * m.Fz;
+        base = fmaf(-gFo * c1, vz, base);
+        mze = fmaf(2.f, gFo, mz);
+        mzo = mz + gFo;
+    }
     // forcing coefficients
-    const float gF = ph.guo_pref * m.Fz;     // Guo / HCZ: (1 - 1/(2 tau)) F_z
+    const float gF = ph.guo_pref * m.Fz;     // HCZ: (1 - 1/(2 tau)) F_z
     const float du = fmaf(m.Fz, m.dirho, m.Fz);  // EDM: velocity increment F/rho (z only)
     const float dusq = du * (2.f * vz + du); // |v + du|^2 - |v|^2
 
     // rest slot (e = 0), with the exact FP32 weight-sum residual
     {
         float heq = LF::w(0) * base + LF::kMassCorr * m.drho + LF::kUsqCorr * (mx * vx + my * vy + mz * vz);
-        float F0 = 0.f;
-        if constexpr (FORCING == kGuo) F0 = -gF * LF::w(0) * c1 * vz;
+        float F0 = 0.f;   // (Guo: folded into base)
         if constexpr (FORCING == kHCZ) F0 = -gF * c1 * vz * LF::w(0) * (1.f - c0 * vsq);
         if constexpr (FORCING == kEDM) {
             const float rdusq = fmaf(m.drho, dusq, dusq);   // rho (|v + du|^2 - |v|^2)
@@ -448,14 +460,10 @@ LBM_HD void collide_f(float* h, const Macro& m, const Phys& ph)
         constexpr float w = LF::w(i);
         constexpr int ez = LF::ez(i);
         const float eu = e_dot<LF, i>(vx, vy, vz);
-        const float em = e_dot<LF, i>(mx, my, mz);
+        const float em = e_dot<LF, i>(mx, my, mze);
         const float hs = w * fmaf(c2 * em, eu, base);
         float Fs = 0.f, Fa = 0.f;
-        if constexpr (FORCING == kGuo) {
-            // (1 - 1/(2 tau)) w [ (e - u)/cs^2 + (e.u) e / cs^4 ] . F
-            Fs = gF * w * (ez != 0 ? (2.f * c2 * eu * (float)ez - c1 * vz) : -c1 * vz);
-            Fa = gF * w * c1 * (float)ez;
-        } else if constexpr (FORCING == kHCZ) {
+        if constexpr (FORCING == kHCZ) {
             // (1 - 1/(2 tau)) (e - u).F / (rho cs^2) f_eq, f_eq = w rho (1 + P)
             const float ps = 1.f + c2 * eu * eu - c0 * vsq;
             const float pa = c1 * eu;
@@ -478,15 +486,15 @@ LBM_HD void collide_f(float* h, const Macro& m, const Phys& ph)
     };
     sfor<3, kPairs<LF>>([&](auto mc) {
         constexpr int i = 2 * decltype(mc)::value + 1;
-        const float ha = LF::w(i) * c1 * e_dot<LF, i>(mx, my, mz);
+        const float ha = LF::w(i) * c1 * e_dot<LF, i>(mx, my, mzo);
         if constexpr (LF::ex(i) != 0) ox += (float)LF::ex(i) * ha;
         if constexpr (LF::ey(i) != 0) oy += (float)LF::ey(i) * ha;
         if constexpr (LF::ez(i) != 0) oz += (float)LF::ez(i) * ha;
         relax_pair(mc, ha);
     });
-    relax_pair(std::integral_constant<int, 0>{}, fmaf(0.5f, mx, -ox));   // slots 1, 2: +-x
-    relax_pair(std::integral_constant<int, 1>{}, fmaf(0.5f, my, -oy));   // slots 3, 4: +-y
-    relax_pair(std::integral_constant<int, 2>{}, fmaf(0.5f, mz, -oz));   // slots 5, 6: +-z
+    relax_pair(std::integral_constant<int, 0>{}, fmaf(0.5f, mx, -ox));    // slots 1, 2: +-x
+    relax_pair(std::integral_constant<int, 1>{}, fmaf(0.5f, my, -oy));    // slots 3, 4: +-y
+    relax_pair(std::integral_constant<int, 2>{}, fmaf(0.5f, mzo, -oz));   // slots 5, 6: +-z
 }
 
 // g collision (Eqs. 11, 12, 14, 15): g_eq = (rho' + rho0) Theta(u), S_i = w_i (-u_z beta).

@@ -359,20 +359,25 @@ def test_16bit_odd_nx_one_node_kernel_against_oracle(storage, shape):
         assert np.max(np.abs(gg - go)) <= 4 * ulp * np.max(np.abs(dg)) + 2.0 ** -23
 
 
-@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("storage,n,staging", [("fp32", 40, False), ("fp16", 40, False), ("fp16", 33, False),
+                                               ("bf16", 64, True)])
 @pytest.mark.parametrize("pair", ["27x19", "19x7"])
-def test_fused_step_diagnostics_match_separate_calls(storage, pair):
+def test_fused_step_diagnostics_match_separate_calls(storage, n, staging, pair):
     """lbm_step_diagnostics (diagnostics reduced inside the first step) equals
     lbm_diagnostics followed by lbm_step on the same state. FP32 storage: the
     same FP32 node values summed per step-kernel block instead of per
     diagnostics block, so within 1e-9 relative; 16-bit storage: the node
     moments come from the step's short-form FP32 arithmetic, so within 1e-6
     (momentum, which cancels, 1e-6 absolute). The state afterwards is within
-    FP32 rounding of the plain steps, at both AA parities."""
-    n = 40
+    FP32 rounding of the plain steps, at both AA parities. Covers the one-node
+    (odd n) and two-node 16-bit kernels, and tile staging switched on (the
+    diagnosing step then runs the two-node kernel, the others the staged one)."""
     p = lbm.lbm_params_from_physics(n, n, n, pair, "sc", 200.0, 0.2, 1.0, 0.04)
     a = gpu_sim(p, storage)
     b = gpu_sim(p, storage)
+    if staging:
+        for s in (a, b):
+            lbm.lbm_set_tile_staging(s.h, True)
     for s in (a, b):
         s.init_tgv(seed=5, noise_amp=0.01)
         s.step(3)   # odd layout
@@ -391,7 +396,7 @@ def test_fused_step_diagnostics_match_separate_calls(storage, pair):
         fb, gb = b.populations()
         qf, _ = lbm.PAIR_Q[p.pair]
         _, wf, _ = lbm.lbm_velocity_set(qf)
-        tol = 1e-6 if storage == "fp32" else 2.0 ** -9
+        tol = {"fp32": 1e-6, "fp16": 2.0 ** -9, "bf16": 2.0 ** -6}[storage]
         assert np.all(np.abs(fa - fb) <= tol * np.max(np.abs(fb - wf[:, None])) + 1e-12)
         assert np.all(np.abs(ga - gb) <= tol * np.max(np.abs(gb)) + 1e-12)
     with pytest.raises(lbm.LbmError):
