@@ -552,19 +552,22 @@ LBM_HD void collide_f_fast(float* h, const Macro& m, const Phys& ph)
         mz = m.jz;
     }
     const float mv = (mx * mx + my * my + mz * mz) * m.irho;       // rho |v|^2
-    const float base = m.drho - c0 * mv;
+    float base = m.drho - c0 * mv;
+    // forcing (Eqs. 8-10 and the cited schemes); v = j_eq / rho
+    const float vz = mz * m.irho;
+    // Guo folded into the equilibrium as in collide_f: base - (tau - 1/2) F_z v_z / cs^2,
+    // e.j + 2 (tau - 1/2) F_z e_z in the even part, e.j + (tau - 1/2) F_z e_z in the odd part
+    const float gFo = (FORCING == kGuo) ? ph.guo_tau * m.Fz : 0.f;
+    if constexpr (FORCING == kGuo) base = fmaf(-gFo * c1, vz, base);
     const float ob = om * base;               // omega (f_eq_i - w_i) / w_i without the e terms
     const float o2 = om * c2 * m.irho;        // omega rho (e.v)^2 / (2 cs^4) per (e.j)^2
     const float o1 = om * c1;                 // omega rho e.v / cs^2 per e.j
-    // forcing (Eqs. 8-10 and the cited schemes); v = j_eq / rho
-    const float vz = mz * m.irho;
     const float gF = ph.guo_pref * m.Fz;
     const float du = m.Fz * m.irho;
     const float dusq = du * (2.f * vz + du);
     {
         const float heq = LF::w(0) * base + LF::kMassCorr * m.drho + LF::kUsqCorr * mv;
-        float F0 = 0.f;
-        if constexpr (FORCING == kGuo) F0 = -gF * LF::w(0) * c1 * vz;
+        float F0 = 0.f;   // (Guo: folded into base)
         if constexpr (FORCING == kHCZ) {
             const float vsq = mv * m.irho;
             F0 = -gF * c1 * vz * LF::w(0) * (1.f - c0 * vsq);
@@ -578,13 +581,16 @@ LBM_HD void collide_f_fast(float* h, const Macro& m, const Phys& ph)
         constexpr float w = LF::w(i);
         constexpr int ez = LF::ez(i);
         const float em = e_dot<LF, i>(mx, my, mz);
-        float hs = fmaf((w * o2) * em, em, w * ob);
+        float emo = em;          // e.j of the odd part
+        float hs;
+        if constexpr (FORCING == kGuo && ez != 0) {
+            hs = fmaf((w * o2) * em, fmaf(2.f * (float)ez, gFo, em), w * ob);
+            emo = fmaf((float)ez, gFo, em);
+        } else {
+            hs = fmaf((w * o2) * em, em, w * ob);
+        }
         float ha = 0.f;          // forcing part of the odd term; the equilibrium part is (w o1) e.j
-        if constexpr (FORCING == kGuo) {
-            const float eu = em * m.irho;
-            hs += gF * w * (ez != 0 ? (2.f * c2 * eu * (float)ez - c1 * vz) : -c1 * vz);
-            ha += gF * w * c1 * (float)ez;
-        } else if constexpr (FORCING == kHCZ) {
+        if constexpr (FORCING == kHCZ) {
             const float eu = em * m.irho;
             const float ps = 1.f + c2 * eu * eu - c0 * mv * m.irho;
             const float pa = c1 * eu;
@@ -598,12 +604,12 @@ LBM_HD void collide_f_fast(float* h, const Macro& m, const Phys& ph)
             if constexpr (ez != 0) ha += w * c1 * (float)ez * m.Fz;
         }
         float hp = hs, hm = hs;
-        if constexpr (FORCING != kShanChen) {
+        if constexpr (FORCING == kHCZ || FORCING == kEDM) {
             hp = hs + ha;
             hm = hs - ha;
         }
-        h[i] = fmaf(cm, h[i], fmaf(w * o1, em, hp));
-        h[j] = fmaf(cm, h[j], fmaf(-(w * o1), em, hm));
+        h[i] = fmaf(cm, h[i], fmaf(w * o1, emo, hp));
+        h[j] = fmaf(cm, h[j], fmaf(-(w * o1), emo, hm));
     });
 }
 
