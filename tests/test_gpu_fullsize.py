@@ -93,8 +93,12 @@ STORE_ABS = {"fp32": 0.0, "fp16": 2.0 ** -24, "bf16": 0.0}
     (256, "27x19", "sc", 800.0, 0.1, "fp16"),
     (256, "27x19", "sc", 800.0, 0.1, "bf16"),
     (128, "19x7", "guo", 400.0, 0.5, "fp32"),    # 128^3 stencil/forcing sweep
+    (128, "19x7", "sc", 400.0, 0.1, "fp32"),
+    (128, "27x19", "guo", 400.0, 0.5, "fp32"),
+    (128, "27x19", "sc", 400.0, 0.1, "fp32"),
     (128, "27x19", "edm", 400.0, 0.1, "fp32"),
     (512, "27x19", "sc", 1600.0, 0.1, "fp16"),   # 512^3 capacity case
+    (512, "27x19", "sc", 1600.0, 0.1, "fp32"),   # 24.7 GB of populations
 ])
 def test_sampled_parity_full_size(n, pair, forcing, Re, Fr, storage):
     p = lbm.lbm_params_from_physics(n, n, n, pair, forcing, Re, Fr, 1.0, 0.04)
