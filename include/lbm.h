@@ -159,7 +159,16 @@ int lbm_required_bytes(lbm_handle h, size_t* bytes);
 
 /* Use caller-owned device memory (>= lbm_required_bytes, 256-byte aligned,
  * on the handle's device) as the population store; the caller keeps
- * ownership and must keep it alive until lbm_destroy. Must precede init. */
+ * ownership and must keep it alive until lbm_destroy. Must precede init.
+ * Store layout: the Q_f f arrays, then the Q_g g arrays, each of nx*ny*nz
+ * elements holding the deviations f_i - w_i and g_i - w_i rho0 (FP32, or
+ * FP16 / BF16 per lbm_storage), z-major then y, one x-row contiguous. Within
+ * a row node x sits at position x, except in 16-bit stores with even nx,
+ * which keep the half-row order: position 2 x for x < nx/2 and
+ * 2 (x - nx/2) + 1 otherwise, so that 32-bit word k of a row holds nodes k
+ * and k + nx/2. After an odd number of steps the slots are in the swapped
+ * AA arrangement; lbm_get_populations / lbm_set_populations read and write
+ * node order in either case. */
 int lbm_attach(lbm_handle h, void* device_ptr, size_t bytes);
 
 /* Eq. 20 initial state (Section 2.4): u = U0 (sin x cos y cos z,

@@ -171,8 +171,42 @@ struct Geometry {
     uint32_t n3;      // nx * ny * nz
 };
 
+// Order of the nodes of one row within each slot array. FP32 stores, and
+// 16-bit stores with odd nx: node x at position x. 16-bit stores with even nx
+// (half-row order, half = nx / 2): position 2 (x mod half) + (x >= half), so
+// the 32-bit word w of a row holds nodes w (low half) and w + half (high
+// half). A shift of the row by one node then moves both nodes of every word
+// to the next word, so the two-nodes-per-thread kernel reads and writes whole
+// aligned words on both AA steps; only where the row wraps (words 0 and
+// half - 1) the two halves arrive exchanged.
+__host__ __device__ __forceinline__ int row_pos(int x, int half)
+{
+    return half == 0 ? x : (x < half ? 2 * x : 2 * (x - half) + 1);
+}
+
+// half of a 16-bit store: nx / 2 for even nx, 0 (node order) for odd nx.
+__host__ __device__ __forceinline__ int row_half(const Geometry& g)
+{
+    return (g.nx & 1) ? 0 : g.nx / 2;
+}
+
+// Element index, within a slot array of a 16-bit store, of the node with
+// linear index idx.
+__host__ __device__ __forceinline__ uint32_t store_index(const Geometry& g, uint32_t idx)
+{
+    const int half = row_half(g);
+    if (half == 0) return idx;
+    const int x = (int)(idx % (uint32_t)g.nx);
+    return idx - (uint32_t)x + (uint32_t)row_pos(x, half);
+}
+
 // Neighbour offsets of one node with periodic wrap. off(s) with s = (sx, sy, sz)
-// in {-1, 0, 1}^3 is the linear index of node (x + sx, y + sy, z + sz).
+// in {-1, 0, 1}^3 is the element index, within a slot array, of node
+// (x + sx, y + sy, z + sz): its linear index, or with a row order (half > 0)
+// the row's start plus the node's position in the row.
+struct RowOrder {
+    int half;
+};
 struct NodeAddr {
     uint32_t X[3], Y[3], Z[3];
     __device__ __forceinline__ NodeAddr(const Geometry& g, int x, int y, int z)
@@ -185,11 +219,38 @@ struct NodeAddr {
         Y[0] = ym * g.nx; Y[1] = y * g.nx; Y[2] = yp * g.nx;
         Z[0] = zm * nxy; Z[1] = z * nxy; Z[2] = zp * nxy;
     }
+    __device__ __forceinline__ NodeAddr(const Geometry& g, int x, int y, int z, RowOrder r) : NodeAddr(g, x, y, z)
+    {
+        X[0] = row_pos((int)X[0], r.half);
+        X[1] = row_pos(x, r.half);
+        X[2] = row_pos((int)X[2], r.half);
+    }
     __device__ __forceinline__ uint32_t off(int sx, int sy, int sz) const
     {
         return Z[sz + 1] + Y[sy + 1] + X[sx + 1];
     }
 };
+
+// NodeAddr in the order of a store of element type T: FP32 stores are never
+// reordered, so their addressing has no run-time row order at all.
+template <class T>
+__device__ __forceinline__ NodeAddr node_addr(const Geometry& g, int x, int y, int z)
+{
+    if constexpr (std::is_same_v<T, float>) {
+        return NodeAddr(g, x, y, z);
+    } else {
+        return NodeAddr(g, x, y, z, RowOrder{row_half(g)});
+    }
+}
+template <class T>
+__host__ __device__ __forceinline__ uint32_t store_index_t(const Geometry& g, uint32_t idx)
+{
+    if constexpr (std::is_same_v<T, float>) {
+        return idx;
+    } else {
+        return store_index(g, idx);
+    }
+}
 
 // AA pattern, in place. Natural layout (after an even number of steps): slot i at
 // node x holds f_i(x). The even step reads slot i at x and writes the

@@ -239,7 +239,7 @@ template <class P, int FORCING, class T, bool ODD, class Hook>
 __device__ __forceinline__ void update_node(void* fv, void* gv, const Geometry& geo, const Phys& ph, int x,
                                             int y, int z, Hook&& hook)
 {
-    const NodeAddr a(geo, x, y, z);
+    const NodeAddr a = node_addr<T>(geo, x, y, z);
     T* __restrict__ f = static_cast<T*>(fv);
     T* __restrict__ g = static_cast<T*>(gv);
     const uint32_t n3 = geo.n3;
@@ -248,7 +248,7 @@ __device__ __forceinline__ void update_node(void* fv, void* gv, const Geometry& 
     load_node<typename P::LF, ODD, T>(f, n3, a, h);
     load_node<typename P::LG, ODD, T>(g, n3, a, k);
     collide_node<P, FORCING, kExact>(h, k, ph, hook);
-    const NodeAddr b(geo, (int)launder(x), (int)launder(y), (int)launder(z));
+    const NodeAddr b = node_addr<T>(geo, (int)launder(x), (int)launder(y), (int)launder(z));
     store_node<typename P::LF, ODD, T>(f, n3, b, h);
     store_node<typename P::LG, ODD, T>(g, n3, b, k);
 }
@@ -300,27 +300,29 @@ __global__ void __launch_bounds__(256, 2) k_step_diag(StepArgs args)
 }
 
 // ---------------------------------------------------------------------------
-// 16-bit storage, two x-adjacent nodes per thread, nx even. Thread t takes
-// x0 = 2 t and the nodes (x0, x0 + 1) on even steps, (x0 - 1, x0) on odd
-// steps (x0 - 1 wrapped), low half first. The pair's values of one slot are
-// then one aligned 32-bit word for every slot of the even step and for the
-// e_x != 0 slots of the odd step, whose AA accesses at x -+ e_x land on
-// (x0 - 2, x0 - 1) or (x0, x0 + 1); the odd step's e_x = 0 slots are two
-// 16-bit accesses. Loads, stores and address arithmetic are shared by the two
-// nodes, and the two results of a slot are packed by one conversion.
+// 16-bit storage, two nodes per thread, nx even, in the half-row order of the
+// store (row_pos): thread k < half takes the 32-bit word k of its row, nodes
+// k (low half) and k + half (high half), on both AA steps. The odd step reads
+// slot opp(i) at x - e_i and writes slot i at x + e_i; both nodes move by the
+// same e_x, so every access is the aligned word k - e_x or k + e_x of a
+// neighbouring row. Where the row wraps the word arrives with its halves
+// exchanged: word half - 1 read from k = 0 (e_x = 1) and written from k = 0
+// (e_x = -1), word 0 read from k = half - 1 (e_x = -1) and written from
+// k = half - 1 (e_x = 1). Those lanes exchange the halves in registers, in
+// code that only the warps holding word 0 or word half - 1 run. Loads, stores
+// and address arithmetic are shared by the two nodes.
 // ---------------------------------------------------------------------------
 template <class T>
 struct Pack16;
 template <>
 struct Pack16<__half> {
-    static __device__ __forceinline__ float lo(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
-    static __device__ __forceinline__ float hi(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+    static __device__ __forceinline__ float lo(uint32_t w) { return __low2float(*reinterpret_cast<const __half2*>(&w)); }
+    static __device__ __forceinline__ float hi(uint32_t w) { return __high2float(*reinterpret_cast<const __half2*>(&w)); }
     static __device__ __forceinline__ uint32_t pack(float a, float b)
     {
         const __half2 v = __floats2half2_rn(a, b);
         return *reinterpret_cast<const uint32_t*>(&v);
     }
-    static __device__ __forceinline__ uint32_t bits(float a) { return __half_as_ushort(__float2half_rn(a)); }
 };
 template <>
 struct Pack16<__nv_bfloat16> {
@@ -331,30 +333,48 @@ struct Pack16<__nv_bfloat16> {
         const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
         return *reinterpret_cast<const uint32_t*>(&v);
     }
-    static __device__ __forceinline__ uint32_t bits(float a) { return __bfloat16_as_ushort(__float2bfloat16_rn(a)); }
 };
 
-// Element offsets around the pair: X[0] = x0 - 2, X[1] = x0 - 1 (both
-// wrapped), X[2] = x0; Y and Z for y -1, 0, +1 and z -1, 0, +1.
+// Element offsets of the words around the pair's word k within one slot
+// array: X[0] = word k - 1, X[1] = word k + 1 (both wrapped), X[2] = word k
+// (element 2 k = x0); Y and Z for y -1, 0, +1 and z -1, 0, +1.
 struct PairAddr {
     uint32_t X[3], Y[3], Z[3];
     __device__ __forceinline__ PairAddr(const Geometry& g, int x0, int y, int z)
     {
-        const int xm2 = (x0 == 0) ? g.nx - 2 : x0 - 2;
-        const int xm1 = (x0 == 0) ? g.nx - 1 : x0 - 1;
+        const int wm = (x0 == 0) ? g.nx - 2 : x0 - 2;
+        const int wp = (x0 == g.nx - 2) ? 0 : x0 + 2;
         const int ym = (y == 0) ? g.ny - 1 : y - 1, yp = (y == g.ny - 1) ? 0 : y + 1;
         const int zm = (z == 0) ? g.nz - 1 : z - 1, zp = (z == g.nz - 1) ? 0 : z + 1;
         const uint32_t nxy = (uint32_t)g.nx * (uint32_t)g.ny;
-        X[0] = xm2; X[1] = xm1; X[2] = x0;
+        X[0] = wm; X[1] = wp; X[2] = x0;
         Y[0] = ym * g.nx; Y[1] = y * g.nx; Y[2] = yp * g.nx;
         Z[0] = zm * nxy; Z[1] = z * nxy; Z[2] = zp * nxy;
     }
     __device__ __forceinline__ uint32_t off(int p, int sy, int sz) const { return Z[sz + 1] + Y[sy + 1] + X[p]; }
 };
 
+// The seam lanes of a pair: k = 0 (first) and k = half - 1 (last), and
+// whether any lane of the warp is one (a warp-uniform branch condition).
+struct Seam {
+    bool first, last, warp_first, warp_last;
+    __device__ __forceinline__ Seam(const Geometry& g, int x0)
+    {
+        first = x0 == 0;
+        last = x0 == g.nx - 2;
+        const unsigned m = __activemask();
+        warp_first = __any_sync(m, first);
+        warp_last = __any_sync(m, last);
+    }
+};
+
+__device__ __forceinline__ uint32_t swap_halves(uint32_t w) { return __byte_perm(w, 0u, 0x1032); }
+
+// Loads default-cached: the odd step writes each word back shortly after
+// reading it, and a word still in L2 takes the write without a miss.
 __device__ __forceinline__ uint32_t ld_word(const unsigned short* p)
 {
-    return __ldcs(reinterpret_cast<const unsigned int*>(p));
+    return *reinterpret_cast<const unsigned int*>(p);
 }
 __device__ __forceinline__ void st_word(unsigned short* p, uint32_t w)
 {
@@ -363,61 +383,92 @@ __device__ __forceinline__ void st_word(unsigned short* p, uint32_t w)
 
 template <class L, bool ODD>
 __device__ __forceinline__ void load_pair(const unsigned short* __restrict__ b16, uint32_t n3, const PairAddr& a,
-                                          uint32_t* w)
+                                          const Seam& sm, uint32_t* w)
 {
     sfor<0, L::kQ>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
         if constexpr (!ODD) {
-            w[i] = ld_word(b16 + ((uint32_t)i * n3 + a.off(2, 0, 0)));
+            w[i] = ld_word(b16 + (size_t)i * n3 + a.off(2, 0, 0));
         } else {
-            // nodes x0 - 1 and x0 read slot opp(i) at x - e_i
-            const uint32_t s = (uint32_t)L::opp(i) * n3;
-            if constexpr (ex == 1) {
-                w[i] = ld_word(b16 + (s + a.off(0, -ey, -ez)));   // (x0 - 2, x0 - 1)
-            } else if constexpr (ex == -1) {
-                w[i] = ld_word(b16 + (s + a.off(2, -ey, -ez)));   // (x0, x0 + 1)
-            } else {
-                const uint32_t lo = __ldcs(b16 + (s + a.off(1, -ey, -ez)));
-                const uint32_t hi = __ldcs(b16 + (s + a.off(2, -ey, -ez)));
-                w[i] = lo | (hi << 16);
-            }
+            // slot opp(i) at x - e_i: word k - e_x
+            constexpr int p = ex == 1 ? 0 : ex == -1 ? 1 : 2;
+            w[i] = ld_word(b16 + ((uint32_t)L::opp(i) * n3 + a.off(p, -ey, -ez)));
         }
     });
+    if constexpr (ODD) {
+        if (sm.warp_first) {
+            sfor<0, L::kQ>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                if constexpr (L::ex(i) == 1) w[i] = sm.first ? swap_halves(w[i]) : w[i];
+            });
+        }
+        if (sm.warp_last) {
+            sfor<0, L::kQ>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                if constexpr (L::ex(i) == -1) w[i] = sm.last ? swap_halves(w[i]) : w[i];
+            });
+        }
+    }
 }
 
 template <class L, bool ODD>
 __device__ __forceinline__ void store_pair(unsigned short* __restrict__ b16, uint32_t n3, const PairAddr& a,
-                                           const uint32_t* w)
+                                           const Seam& sm, uint32_t* w)
 {
+    if constexpr (ODD) {
+        if (sm.warp_first) {
+            sfor<0, L::kQ>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                if constexpr (L::ex(i) == -1) w[i] = sm.first ? swap_halves(w[i]) : w[i];
+            });
+        }
+        if (sm.warp_last) {
+            sfor<0, L::kQ>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                if constexpr (L::ex(i) == 1) w[i] = sm.last ? swap_halves(w[i]) : w[i];
+            });
+        }
+    }
     sfor<0, L::kQ>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
         if constexpr (!ODD) {
-            st_word(b16 + ((uint32_t)L::opp(i) * n3 + a.off(2, 0, 0)), w[i]);
+            st_word(b16 + (size_t)L::opp(i) * n3 + a.off(2, 0, 0), w[i]);
         } else {
-            // nodes x0 - 1 and x0 write slot i at x + e_i
-            const uint32_t s = (uint32_t)i * n3;
-            if constexpr (ex == 1) {
-                st_word(b16 + (s + a.off(2, ey, ez)), w[i]);      // (x0, x0 + 1)
-            } else if constexpr (ex == -1) {
-                st_word(b16 + (s + a.off(0, ey, ez)), w[i]);      // (x0 - 2, x0 - 1)
-            } else {
-                __stcs(b16 + (s + a.off(1, ey, ez)), (unsigned short)(w[i] & 0xffffu));
-                __stcs(b16 + (s + a.off(2, ey, ez)), (unsigned short)(w[i] >> 16));
-            }
+            // slot i at x + e_i: word k + e_x
+            constexpr int p = ex == 1 ? 1 : ex == -1 ? 0 : 2;
+            st_word(b16 + ((uint32_t)i * n3 + a.off(p, ey, ez)), w[i]);
         }
     });
 }
 
-// Both nodes of a pair, in place on the packed words: the low-half node, then
-// the high-half node. Each result goes back into its half of the word before
-// the other node is unpacked, so only one node's values are live in FP32.
+// Both nodes of a pair on the packed words: the low-half node, then the
+// high-half node. Each node's results are packed two slots to a word by one
+// conversion (slots 2m, 2m + 1; the last slot of an odd count alone); once
+// the high-half node is unpacked the loaded words are dead, so at most one
+// node's FP32 values and the other's packed results are live. One byte
+// permute per slot then forms the stored words (low node, high node).
 // hook(which, h, m) sees node `which` (0 low, 1 high) between its moments
 // and its collisions.
+template <int Q, class T>
+__device__ __forceinline__ void pack_slots(const float* h, uint32_t* t)
+{
+#pragma unroll
+    for (int i = 0; i < Q / 2; ++i) t[i] = Pack16<T>::pack(h[2 * i], h[2 * i + 1]);
+    if constexpr (Q % 2) t[Q / 2] = Pack16<T>::pack(h[Q - 1], 0.f);
+}
+template <int Q>
+__device__ __forceinline__ void merge_slots(const uint32_t* tlo, const uint32_t* thi, uint32_t* w)
+{
+#pragma unroll
+    for (int i = 0; i < Q; ++i) w[i] = __byte_perm(tlo[i / 2], thi[i / 2], (i & 1) ? 0x7632 : 0x5410);
+}
+
 template <class P, int FORCING, class T, class Hook>
 __device__ __forceinline__ void collide_pair_words(uint32_t* wf, uint32_t* wg, const Phys& ph, Hook&& hook)
 {
+    uint32_t tf[(P::QF + 1) / 2], tg[(P::QG + 1) / 2];
     {
         float h[P::QF], k[P::QG];
 #pragma unroll
@@ -425,10 +476,8 @@ __device__ __forceinline__ void collide_pair_words(uint32_t* wf, uint32_t* wg, c
 #pragma unroll
         for (int i = 0; i < P::QG; ++i) k[i] = Pack16<T>::lo(wg[i]);
         collide_node<P, FORCING, false>(h, k, ph, [&](const float* hh, const Macro& m) { hook(0, hh, m); });
-#pragma unroll
-        for (int i = 0; i < P::QF; ++i) wf[i] = __byte_perm(wf[i], Pack16<T>::bits(h[i]), 0x3254);
-#pragma unroll
-        for (int i = 0; i < P::QG; ++i) wg[i] = __byte_perm(wg[i], Pack16<T>::bits(k[i]), 0x3254);
+        pack_slots<P::QF, T>(h, tf);
+        pack_slots<P::QG, T>(k, tg);
     }
     {
         float h[P::QF], k[P::QG];
@@ -437,10 +486,11 @@ __device__ __forceinline__ void collide_pair_words(uint32_t* wf, uint32_t* wg, c
 #pragma unroll
         for (int i = 0; i < P::QG; ++i) k[i] = Pack16<T>::hi(wg[i]);
         collide_node<P, FORCING, false>(h, k, ph, [&](const float* hh, const Macro& m) { hook(1, hh, m); });
-#pragma unroll
-        for (int i = 0; i < P::QF; ++i) wf[i] = __byte_perm(wf[i], Pack16<T>::bits(h[i]), 0x5410);
-#pragma unroll
-        for (int i = 0; i < P::QG; ++i) wg[i] = __byte_perm(wg[i], Pack16<T>::bits(k[i]), 0x5410);
+        uint32_t uf[(P::QF + 1) / 2], ug[(P::QG + 1) / 2];
+        pack_slots<P::QF, T>(h, uf);
+        pack_slots<P::QG, T>(k, ug);
+        merge_slots<P::QF>(tf, uf, wf);
+        merge_slots<P::QG>(tg, ug, wg);
     }
 }
 
@@ -458,15 +508,16 @@ __device__ __forceinline__ void update_pair(const StepArgs& args, int x0, int y,
     unsigned short* fb = static_cast<unsigned short*>(args.f);
     unsigned short* gb = static_cast<unsigned short*>(args.g);
     uint32_t wf[P::QF], wg[P::QG];
+    const Seam sm(args.geo, x0);
     {
         const PairAddr a(args.geo, x0, y, z);
-        load_pair<typename P::LF, ODD>(fb, n3, a, wf);
-        load_pair<typename P::LG, ODD>(gb, n3, a, wg);
+        load_pair<typename P::LF, ODD>(fb, n3, a, sm, wf);
+        load_pair<typename P::LG, ODD>(gb, n3, a, sm, wg);
     }
     collide_pair_words<P, FORCING, T>(wf, wg, args.ph, hook);
     const PairAddr b(args.geo, (int)launder(x0), (int)launder(y), (int)launder(z));
-    store_pair<typename P::LF, ODD>(fb, n3, b, wf);
-    store_pair<typename P::LG, ODD>(gb, n3, b, wg);
+    store_pair<typename P::LF, ODD>(fb, n3, b, sm, wf);
+    store_pair<typename P::LG, ODD>(gb, n3, b, sm, wg);
 }
 
 // Two 256-thread blocks per SM (<= 128 registers) for D3Q27xD3Q19, whose 46
@@ -496,9 +547,9 @@ __global__ void __launch_bounds__(256, 2) k_step2_diag(StepArgs args)
     DiagAcc d;
     if (x0 < args.geo.nx && y < args.geo.ny) {
         const uint32_t row = (uint32_t)args.geo.nx * ((uint32_t)y + (uint32_t)args.geo.ny * (uint32_t)z);
-        // nodes of the pair: (x0, x0 + 1) even, (x0 - 1, x0) odd
-        const uint32_t lo = row + (uint32_t)(ODD ? (x0 == 0 ? args.geo.nx - 1 : x0 - 1) : x0);
-        const uint32_t hi = row + (uint32_t)(ODD ? x0 : x0 + 1);
+        // nodes of the pair's word k = x0 / 2: k and k + half
+        const uint32_t lo = row + (uint32_t)(x0 / 2);
+        const uint32_t hi = lo + (uint32_t)(args.geo.nx / 2);
         update_pair<P, FORCING, T, ODD>(args, x0, y, z, [&](int which, const float* h, const Macro& m) {
             diag_node<P, false>(h, m, args.dg, args.geo.n3, which ? hi : lo, d);
         });
@@ -594,17 +645,18 @@ __global__ void k_init_fields(InitArgs a)
         eq_dev<LG>((float)rp, (float)(rp + a.rho0), (float)ux, (float)uy, (float)uz, hg);
         T* f = static_cast<T*>(a.f);
         T* g = static_cast<T*>(a.g);
+        const uint32_t sidx = store_index_t<T>(a.geo, idx);
         sfor<0, P::QF>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             float v = hf[i];
             if (a.xi_f) v += a.amp_f * LF::w(i) * (float)a.xi_f[(size_t)canon_code<LF>(i) * n3 + idx];
-            st_pop<T>(f + (size_t)i * n3 + idx, v);
+            st_pop<T>(f + (size_t)i * n3 + sidx, v);
         });
         sfor<0, P::QG>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             float v = hg[i];
             if (a.xi_g) v += a.amp_f * LG::w(i) * (float)a.xi_g[(size_t)canon_code<LG>(i) * n3 + idx];
-            st_pop<T>(g + (size_t)i * n3 + idx, v);
+            st_pop<T>(g + (size_t)i * n3 + sidx, v);
         });
     }
 }
@@ -658,13 +710,14 @@ __global__ void k_init_tgv(TgvArgs a)
         eq_dev<LG>(0.f, (float)a.rho0, (float)ux, (float)uy, (float)uz, hg);
         T* f = static_cast<T*>(a.f);
         T* g = static_cast<T*>(a.g);
+        const uint32_t sidx = store_index_t<T>(a.geo, idx);
         sfor<0, P::QF>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            st_pop<T>(f + (size_t)i * n3 + idx, hf[i]);
+            st_pop<T>(f + (size_t)i * n3 + sidx, hf[i]);
         });
         sfor<0, P::QG>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            st_pop<T>(g + (size_t)i * n3 + idx, hg[i]);
+            st_pop<T>(g + (size_t)i * n3 + sidx, hg[i]);
         });
     }
 }
@@ -690,7 +743,7 @@ __global__ void k_get_pops(PopArgs a)
     for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n3; idx += gridDim.x * blockDim.x) {
         int x, y, z;
         node_xyz(a.geo, idx, x, y, z);
-        const NodeAddr na(a.geo, x, y, z);
+        const NodeAddr na = node_addr<T>(a.geo, x, y, z);
         float h[P::QF], k[P::QG];
         if (a.odd) {
             load_node<LF, true, T>(static_cast<const T*>(a.f), n3, na, h);
@@ -732,7 +785,7 @@ __global__ void k_sample_pops(SampleArgs a)
         const uint32_t idx = (uint32_t)a.nodes[s];
         int x, y, z;
         node_xyz(a.geo, idx, x, y, z);
-        const NodeAddr na(a.geo, x, y, z);
+        const NodeAddr na = node_addr<T>(a.geo, x, y, z);
         float h[P::QF], k[P::QG];
         if (a.odd) {
             load_node<LF, true, T>(static_cast<const T*>(a.f), a.geo.n3, na, h);
@@ -762,13 +815,14 @@ __global__ void k_set_pops(PopArgs a)
     T* f = static_cast<T*>(a.f);
     T* g = static_cast<T*>(a.g);
     for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n3; idx += gridDim.x * blockDim.x) {
+        const uint32_t sidx = store_index_t<T>(a.geo, idx);
         sfor<0, P::QF>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            st_pop<T>(f + (size_t)i * n3 + idx, (float)(a.fout[(size_t)i * n3 + idx] - LF::wd(i)));
+            st_pop<T>(f + (size_t)i * n3 + sidx, (float)(a.fout[(size_t)i * n3 + idx] - LF::wd(i)));
         });
         sfor<0, P::QG>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            st_pop<T>(g + (size_t)i * n3 + idx,
+            st_pop<T>(g + (size_t)i * n3 + sidx,
                       (float)(a.gout[(size_t)i * n3 + idx] - LG::wd(i) * a.rho0));
         });
     }
@@ -784,7 +838,7 @@ __global__ void __launch_bounds__(kDiagBlock) k_diag_moments(DiagArgs a)
     for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n3; idx += gridDim.x * blockDim.x) {
         int x, y, z;
         node_xyz(a.geo, idx, x, y, z);
-        const NodeAddr na(a.geo, x, y, z);
+        const NodeAddr na = node_addr<T>(a.geo, x, y, z);
         float h[P::QF], k[P::QG];
         if (a.odd) {
             load_node<LF, true, T>(static_cast<const T*>(a.f), n3, na, h);
@@ -812,7 +866,7 @@ __global__ void __launch_bounds__(kDiagBlock) k_diag_gradients(DiagArgs a)
     for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n3; idx += gridDim.x * blockDim.x) {
         int x, y, z;
         node_xyz(a.geo, idx, x, y, z);
-        const NodeAddr na(a.geo, x, y, z);
+        const NodeAddr na(a.geo, x, y, z);   // the FP32 fields are in node order
         const uint32_t xp = na.off(1, 0, 0), xm = na.off(-1, 0, 0);
         const uint32_t yp = na.off(0, 1, 0), ym = na.off(0, -1, 0);
         const uint32_t zp = na.off(0, 0, 1), zm = na.off(0, 0, -1);
@@ -964,7 +1018,7 @@ __global__ void k_get_fields(FieldArgs a)
     for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n3; idx += gridDim.x * blockDim.x) {
         int x, y, z;
         node_xyz(a.geo, idx, x, y, z);
-        const NodeAddr na(a.geo, x, y, z);
+        const NodeAddr na = node_addr<T>(a.geo, x, y, z);
         float h[P::QF], k[P::QG];
         if (a.odd) {
             load_node<typename P::LF, true, T>(static_cast<const T*>(a.f), n3, na, h);

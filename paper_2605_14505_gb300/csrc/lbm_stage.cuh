@@ -2,18 +2,20 @@
 // brought into shared memory by bulk asynchronous copies (cp.async.bulk,
 // completion counted on an mbarrier) one tile ahead of the compute.
 //
-// A tile is W = 2 * blockDim.x consecutive nodes of one x-row (y, z). For
+// The store is in half-row order (row_pos): word k of a row holds nodes k and
+// k + nx / 2. A tile is W = 2 * blockDim.x consecutive elements of one x-row
+// (y, z), the words of blockDim.x pairs; thread p takes word xs / 2 + p. For
 // every slot the AA step reads one row segment: slot i of row (y, z) on the
 // even step, slot opp(i) of row (y - e_y, z - e_z) on the odd step. Each such
-// segment is one bulk copy of W elements (even) or W + 8 elements starting 8
-// before the tile (odd: the pairs are (x0 - 1, x0) and read up to two nodes
-// to the left); at x = 0 the 8-element head wraps to the end of the row and
-// is a separate 16-byte copy. Warp 0 issues the copies of tile k + 1 into the
+// segment is one bulk copy of W elements (even) or W + 16 elements from 8
+// before the tile to 8 after it (odd: the words k - 1 and k + 1 are read);
+// at either end of the row the 8-element pad wraps to the other end and is a
+// separate 16-byte copy. Warp 0 issues the copies of tile k + 1 into the
 // other half of a two-stage ring while the block computes tile k from shared
 // memory, so the DRAM latency is covered by the ring rather than by
 // registers held in flight. Results are stored straight to global memory as
-// in k_step2 (aligned 32-bit words, and 16-bit halves for the odd step's
-// e_x = 0 slots). Blocks are persistent: block b takes tiles b, b + grid, ...
+// in k_step2 (aligned 32-bit words). Blocks are persistent: block b takes
+// tiles b, b + grid, ...
 //
 // Every mbarrier wait is bounded (spin_limit polls). A wait that runs out
 // raises *err; the block then waits, again bounded, for its copies still in
@@ -37,13 +39,13 @@ struct StageArgs {
     uint32_t extra_tx;      // test hook: bytes expected beyond the copies (0 in use)
 };
 
-constexpr int kStagePad = 8;   // staged row element j holds x = xs - 8 + j
+constexpr int kStagePad = 8;   // staged row element j holds row element xs - 8 + j
 
-// Shared-memory bytes of one block: two stages of Q rows of W + 8 elements,
+// Shared-memory bytes of one block: two stages of Q rows of W + 16 elements,
 // two mbarriers, Q row codes.
 __host__ __device__ constexpr size_t stage_smem_bytes(int q, int W)
 {
-    return (size_t)2 * q * (W + kStagePad) * 2 + 16 + (size_t)q * 4;
+    return (size_t)2 * q * (W + 2 * kStagePad) * 2 + 16 + (size_t)q * 4;
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
@@ -127,13 +129,13 @@ __device__ __forceinline__ void stage_issue(const StageArgs& A, uint16_t* st, ui
 {
     constexpr int Q = P::QF + P::QG;
     const int lane = threadIdx.x & 31;
-    const int W = A.W, RS = W + kStagePad;
+    const int W = A.W, RS = W + 2 * kStagePad;
     const int nx = A.geo.nx, ny = A.geo.ny, nz = A.geo.nz;
     const uint32_t xt = t % (uint32_t)A.ntx;
     const uint32_t row = t / (uint32_t)A.ntx;
     const int y = (int)(row % (uint32_t)ny), z = (int)(row / (uint32_t)ny);
     const int xs = (int)xt * W;
-    const uint32_t row_bytes = (uint32_t)(ODD ? W + kStagePad : W) * 2u;
+    const uint32_t row_bytes = (uint32_t)(ODD ? W + 2 * kStagePad : W) * 2u;
     if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)Q * row_bytes + A.extra_tx);
     __syncwarp();
     const uint16_t* base = static_cast<const uint16_t*>(A.f);
@@ -148,11 +150,13 @@ __device__ __forceinline__ void stage_issue(const StageArgs& A, uint16_t* st, ui
         uint16_t* dst = st + (size_t)r * RS;
         if (!ODD) {
             bulk_copy_g2s(dst + kStagePad, src + xs, (uint32_t)W * 2u, bar);
-        } else if (xs > 0) {
+        } else if (xs > 0 && xs + W < nx) {
             bulk_copy_g2s(dst, src + (xs - kStagePad), row_bytes, bar);
         } else {
-            bulk_copy_g2s(dst, src + (nx - kStagePad), kStagePad * 2u, bar);
-            bulk_copy_g2s(dst + kStagePad, src, (uint32_t)W * 2u, bar);
+            // head and tail pads wrap at the ends of the row
+            bulk_copy_g2s(dst, src + (xs > 0 ? xs - kStagePad : nx - kStagePad), kStagePad * 2u, bar);
+            bulk_copy_g2s(dst + kStagePad, src + xs, (uint32_t)W * 2u, bar);
+            bulk_copy_g2s(dst + kStagePad + W, src + (xs + W < nx ? xs + W : 0), kStagePad * 2u, bar);
         }
     }
 }
@@ -162,23 +166,31 @@ __device__ __forceinline__ uint32_t lds_word(const uint16_t* p)
     return *reinterpret_cast<const uint32_t*>(p);
 }
 
-// The pair's words of lattice L from its stage rows (row0 = first row of L).
-// Pair p of the tile: nodes (x0, x0 + 1) even, (x0 - 1, x0) odd, x0 = xs + 2p.
+// The pair's words of lattice L from its stage rows (rows = first row of L):
+// word p of the tile on the even step, word p - e_x on the odd step, with the
+// halves exchanged where the row wraps (as load_pair).
 template <class L, bool ODD>
-__device__ __forceinline__ void stage_load(const uint16_t* rows, int RS, int p, uint32_t* w)
+__device__ __forceinline__ void stage_load(const uint16_t* rows, int RS, int p, const Seam& sm, uint32_t* w)
 {
     sfor<0, L::kQ>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
-        constexpr int ex = L::ex(i);
-        const uint16_t* r = rows + i * RS + kStagePad + 2 * p;
-        if constexpr (!ODD || ex == -1) {
-            w[i] = lds_word(r);            // x0, x0 + 1
-        } else if constexpr (ex == 1) {
-            w[i] = lds_word(r - 2);        // x0 - 2, x0 - 1
-        } else {
-            w[i] = (uint32_t)r[-1] | ((uint32_t)r[0] << 16);   // x0 - 1, x0
-        }
+        constexpr int ex = ODD ? L::ex(i) : 0;
+        w[i] = lds_word(rows + i * RS + kStagePad + 2 * p - 2 * ex);
     });
+    if constexpr (ODD) {
+        if (sm.warp_first) {
+            sfor<0, L::kQ>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                if constexpr (L::ex(i) == 1) w[i] = sm.first ? swap_halves(w[i]) : w[i];
+            });
+        }
+        if (sm.warp_last) {
+            sfor<0, L::kQ>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                if constexpr (L::ex(i) == -1) w[i] = sm.last ? swap_halves(w[i]) : w[i];
+            });
+        }
+    }
 }
 
 template <class P>
@@ -189,7 +201,7 @@ __global__ void __launch_bounds__(128, kStageMinBlocks<P>) k_step_staged(const _
 {
     constexpr int Q = P::QF + P::QG;
     extern __shared__ __align__(128) unsigned char smem[];
-    const int W = A.W, RS = W + kStagePad;
+    const int W = A.W, RS = W + 2 * kStagePad;
     uint16_t* stages = reinterpret_cast<uint16_t*>(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)2 * Q * RS * 2);
     uint32_t* code = reinterpret_cast<uint32_t*>(bar + 2);
@@ -219,16 +231,17 @@ __global__ void __launch_bounds__(128, kStageMinBlocks<P>) k_step_staged(const _
         const bool ok = mbar_wait(&bar[s], (k >> 1) & 1u, A.spin_limit);
         if (ok) {
             const uint16_t* st = stages + (size_t)s * Q * RS;
-            uint32_t wf[P::QF], wg[P::QG];
-            stage_load<typename P::LF, ODD>(st, RS, p, wf);
-            stage_load<typename P::LG, ODD>(st + (size_t)P::QF * RS, RS, p, wg);
-            collide_pair_words<P, FORCING, T>(wf, wg, A.ph);
             const uint32_t row = t / (uint32_t)A.ntx;
             const int x0 = (int)(t - row * (uint32_t)A.ntx) * W + 2 * p;
+            const Seam sm(A.geo, x0);
+            uint32_t wf[P::QF], wg[P::QG];
+            stage_load<typename P::LF, ODD>(st, RS, p, sm, wf);
+            stage_load<typename P::LG, ODD>(st + (size_t)P::QF * RS, RS, p, sm, wg);
+            collide_pair_words<P, FORCING, T>(wf, wg, A.ph);
             const int y = (int)(row % (uint32_t)A.geo.ny), z = (int)(row / (uint32_t)A.geo.ny);
             const PairAddr b(A.geo, (int)launder(x0), (int)launder(y), (int)launder(z));
-            store_pair<typename P::LF, ODD>(fb, A.geo.n3, b, wf);
-            store_pair<typename P::LG, ODD>(gb, A.geo.n3, b, wg);
+            store_pair<typename P::LF, ODD>(fb, A.geo.n3, b, sm, wf);
+            store_pair<typename P::LG, ODD>(gb, A.geo.n3, b, sm, wg);
         }
         if (__syncthreads_or(!ok)) {
             // a wait ran out: report, let the copies in flight land, stop

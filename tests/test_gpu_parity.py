@@ -430,3 +430,43 @@ def test_prefetched_initialisation_matches_init_fields():
         fb, gb = b.populations()
         assert np.array_equal(fa, fb) and np.array_equal(ga, gb), k
         assert a.step_count == 5
+
+
+@pytest.mark.parametrize("storage,nx", [("fp16", 6), ("bf16", 8), ("fp16", 5), ("fp32", 6), ("bf16", 2)])
+def test_store_row_order(storage, nx):
+    """The store's element order, which lbm_attach exposes: slot-major, then z,
+    y, and within a row node x at position x (FP32 storage, odd nx) or, for
+    16-bit storage with even nx, the half-row order: position 2 x for
+    x < nx / 2, 2 (x - nx / 2) + 1 above, so that 32-bit word k holds nodes k
+    and k + nx / 2."""
+    import torch
+
+    ny, nz = 3, 2
+    p = lattice_params(nx, ny, nz, "27x19", "sc", 0.55, 0.6, 3e-3 * LAM, -3e-3 / LAM)
+    n3 = nx * ny * nz
+    qf, qg = 27, 19
+    _, wf, _ = lbm.lbm_velocity_set(qf)
+    _, wg, _ = lbm.lbm_velocity_set(qg)
+    # deviations that name their slot and node, exact in every storage type:
+    # multiples of 2^-12 below 2^-4 (8 significant bits at most)
+    code_f = ((np.arange(qf)[:, None] * 7 + np.arange(n3)[None, :] * 3) % 253 + 1) * 2.0 ** -12
+    code_g = -((np.arange(qg)[:, None] * 5 + np.arange(n3)[None, :] * 11) % 251 + 1) * 2.0 ** -12
+    s = gpu_sim(p, storage)
+    s.set_populations(wf[:, None] + code_f, p.rho0 * wg[:, None] + code_g)
+    s.synchronize()
+    dt = {"fp32": torch.float32, "fp16": torch.float16, "bf16": torch.bfloat16}[storage]
+    raw = s._store.view(dt).double().cpu().numpy()
+    rf = raw[: qf * n3].reshape(qf, n3)
+    rg = raw[qf * n3: (qf + qg) * n3].reshape(qg, n3)
+    half = nx // 2 if (storage != "fp32" and nx % 2 == 0) else 0
+    x = np.arange(n3) % nx
+    pos = x if half == 0 else np.where(x < half, 2 * x, 2 * (x - half) + 1)
+    elem = np.arange(n3) - x + pos
+    assert np.array_equal(np.sort(elem), np.arange(n3))
+    assert np.array_equal(rf[:, elem], code_f)
+    assert np.array_equal(rg[:, elem], code_g)
+    # and the library reads its own order back (w + code - w: one FP64 rounding)
+    f, g = s.populations()
+    assert np.max(np.abs(f - wf[:, None] - code_f)) < 1e-12
+    assert np.max(np.abs(g - p.rho0 * wg[:, None] - code_g)) < 1e-12
+    s.close()
