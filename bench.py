@@ -373,8 +373,12 @@ def run_batch_sweep(args, peak):
             "mlups": round(nodes * SWEEP_STEPS / secs / 1e6, 1), "ms_per_step": round(secs * 1e3 / SWEEP_STEPS, 4),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "bytes_per_step": nbytes},
-            "driver": "persistent" if cfg["mode"] == 0 else "per_step", "tile": [cfg["bx"], cfg["by"]],
-            ("grid" if cfg["mode"] == 0 else "tiles"): cfg["grid"], "autotune_ms_per_step": round(tuned_ms, 4),
+            **({"driver": "instances", "launch_shapes": "per instance (autotuned)"} if cfg["mode"] == 2 else
+               {"driver": "persistent" if cfg["mode"] == 0 else "per_step", "tile": [cfg["bx"], cfg["by"]],
+                ("grid" if cfg["mode"] == 0 else "tiles"): cfg["grid"]}),
+            "autotune_ms_per_step": round(tuned_ms, 4),
+            "l2": "achieved counts algorithmic bytes; the per-instance driver runs each instance's steps back "
+                  "to back, so the 32^3-48^3 instances (12-40 MB) are partly served from L2 between steps",
             "all_finite": all(np.isfinite(d["Ek"]) for d in diags), "timing": "host wall clock around 2000 steps"}
 
 
@@ -440,19 +444,25 @@ def run_ncu_case(args):
 
     from paper_2605_14505_gb300 import lbm
 
-    if args.ncu_case == "batch":
-        # the 64-instance sweep, persistent driver, `ncu_steps` steps per launch
+    if args.ncu_case in ("batch", "batch-step"):
+        # the 64-instance sweep: persistent driver, `ncu_steps` steps per launch;
+        # or the per-step driver (one launch per variant and step, below the
+        # graph length, so every launch is a plain one) with its 32 x 2 tiles
         specs = sweep_specs()
         params = [lbm.lbm_params_from_physics(n, n, n, pair, f, Re, Fr, 1.0, U0) for n, pair, f, Re, Fr in specs]
         b = lbm.lbm_batch_create(params)
-        lbm.lbm_batch_set_mode(b, "persistent", args.ncu_steps)
-        lbm.lbm_batch_set_block(b, 32, 8)
+        if args.ncu_case == "batch":
+            lbm.lbm_batch_set_mode(b, "persistent", args.ncu_steps)
+            lbm.lbm_batch_set_block(b, 32, 8)
+        else:
+            lbm.lbm_batch_set_mode(b, "per_step")
+            lbm.lbm_batch_set_block(b, 32, 2)
         lbm.lbm_batch_init_tgv(b, seed=1, noise_amp=1e-3)
         lbm.lbm_batch_step(b, 3 * args.ncu_steps)
         lbm.lbm_batch_synchronize(b)
         lbm.lbm_batch_destroy(b)
         torch.cuda.synchronize()
-        print(json.dumps({"ncu_case": "batch", "steps": 3 * args.ncu_steps, "sources": source_fingerprint()}))
+        print(json.dumps({"ncu_case": args.ncu_case, "steps": 3 * args.ncu_steps, "sources": source_fingerprint()}))
         return
     storage, pair = args.ncu_case, PAIR
     if args.ncu_case.startswith("19x7"):
@@ -480,7 +490,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched sweep")
-    ap.add_argument("--ncu-case", choices=["fp32", "fp16", "bf16", "19x7", "19x7-fp16", "batch"], default=None,
+    ap.add_argument("--ncu-case", choices=["fp32", "fp16", "bf16", "19x7", "19x7-fp16", "batch", "batch-step"],
+                    default=None,
                     help="run a small profiling case instead of the benchmark")
     ap.add_argument("--ncu-n", type=int, default=128)
     ap.add_argument("--ncu-steps", type=int, default=6)

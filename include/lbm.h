@@ -329,17 +329,21 @@ int lbm_destroy(lbm_handle h);
 /* ---- Batched instances -------------------------------------------------
  * A parameter sweep of the paper's kind (Sections 3.2-3.6: stencil pairs,
  * forcing schemes, Froude numbers, resolutions) as many independent periodic
- * lattices. Two drivers: per step, one launch per (pair, forcing) variant
- * over that variant's tiles, replayed from a CUDA graph of 64 steps in which
- * each variant's chain of steps is its own branch (variants share no
- * instance, so the branches overlap); or one persistent cooperative launch
- * per `steps_per_launch` steps over all tiles with a bounded grid barrier
- * between steps. Instances may differ in size, pair (D3Q27xD3Q19,
+ * lattices. Three drivers: per instance, each instance advanced by its own
+ * single-lattice step kernel (its own launch shape), replayed from a CUDA
+ * graph of 64 steps in which every instance's chain of steps is its own
+ * branch (up to 128 branches, largest instances first; instances share no
+ * memory, so the branches overlap and fill each other's tails); per step,
+ * one launch per (pair, forcing) variant over that variant's tiles, replayed
+ * the same way with one branch per variant; or one persistent cooperative
+ * launch per `steps_per_launch` steps over all tiles with a bounded grid
+ * barrier between steps. Instances may differ in size, pair (D3Q27xD3Q19,
  * D3Q19xD3Q7), forcing and parameters; storage is FP32. Each instance's
- * arithmetic is the single-lattice update's. */
+ * arithmetic is the single-lattice update's (bit for bit in the
+ * per-instance driver, which runs the single-lattice kernels). */
 typedef struct lbm_batch_ctx* lbm_batch;
 
-enum lbm_batch_mode { LBM_BATCH_PERSISTENT = 0, LBM_BATCH_PER_STEP = 1 };
+enum lbm_batch_mode { LBM_BATCH_PERSISTENT = 0, LBM_BATCH_PER_STEP = 1, LBM_BATCH_INSTANCES = 2 };
 
 /* Create `count` (1..65535) instances from lattice parameters (copied) and
  * allocate their stores on the current device. LBM_EUNSUPPORTED for a
@@ -358,8 +362,9 @@ int lbm_batch_instance(lbm_batch b, int i, lbm_handle* h);
 int lbm_batch_set_stream(lbm_batch b, void* stream);
 
 /* LBM_BATCH_PERSISTENT (default; steps_per_launch steps per cooperative
- * launch, default 100) or LBM_BATCH_PER_STEP (one launch per step, replayed
- * from a CUDA graph of 64 steps). */
+ * launch, default 100), LBM_BATCH_PER_STEP (one launch per variant and step,
+ * replayed from a CUDA graph of 64 steps) or LBM_BATCH_INSTANCES (each
+ * instance's own step kernel, one graph branch per instance). */
 int lbm_batch_set_mode(lbm_batch b, int mode, int steps_per_launch);
 
 /* Tile shape: bx in {16, 32, 64, 128} nodes along x, by along y, bx*by a
@@ -385,11 +390,12 @@ int lbm_batch_synchronize(lbm_batch b);
  * lbm_batch_synchronize; LBM_ENONFINITE if any instance has NaN/Inf). */
 int lbm_batch_diagnostics(lbm_batch b, lbm_diag* out);
 
-/* Time every tile shape and both modes and keep the fastest: for each
- * candidate one warm-up span, then reps spans timed with CUDA events, a span
- * being one 64-step graph (per-step mode) or one persistent launch of
- * steps_per_launch steps. The instances' state is saved and restored.
- * best_ms_per_step may be NULL. */
+/* Time every tile shape under the per-step and persistent drivers, and the
+ * per-instance driver after lbm_autotune of every instance's launch shape,
+ * and keep the fastest: for each candidate one warm-up span, then reps spans
+ * timed with CUDA events, a span being one 64-step graph (per-step and
+ * per-instance drivers) or one persistent launch of steps_per_launch steps.
+ * The instances' state is saved and restored. best_ms_per_step may be NULL. */
 int lbm_batch_autotune(lbm_batch b, int reps, double* best_ms_per_step);
 
 /* Fault-injection hook for tests of the timeout path: make each grid

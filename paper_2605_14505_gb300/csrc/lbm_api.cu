@@ -1243,6 +1243,12 @@ struct lbm_batch_ctx {
     cudaStream_t vstream[8] = {};
     cudaEvent_t vjoin[8] = {};
     cudaEvent_t vfork = nullptr;
+    // per-instance driver: chain c runs instances chain_of[c] in order, each
+    // with its own single-lattice step kernel; streams and join events are
+    // created on first use
+    std::vector<std::vector<int>> chain_of;
+    std::vector<cudaStream_t> cstream;
+    std::vector<cudaEvent_t> cjoin;
     int bx = 32, by = 8;
     int mode = LBM_BATCH_PERSISTENT;
     int chunk = 100;
@@ -1258,6 +1264,7 @@ struct lbm_batch_ctx {
 namespace {
 
 constexpr int kBatchGraphSteps = 64;
+constexpr int kMaxChains = 128;   // graph branches of the per-instance driver
 
 void batch_drop_graph(lbm_batch_ctx* b)
 {
@@ -1357,6 +1364,52 @@ cudaError_t batch_launch_step(lbm_batch_ctx* b, int odd, cudaStream_t s)
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// Per-instance driver: instances sorted by bytes per step, largest first,
+// dealt round-robin to min(count, kMaxChains) chains, so that the longest
+// chains start first and the chains carry similar work.
+cudaError_t batch_ensure_chains(lbm_batch_ctx* b)
+{
+    if (!b->chain_of.empty()) return cudaSuccess;
+    const int n = (int)b->inst.size();
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    auto bytes = [&](int i) { return b->inst[i]->store_bytes; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return bytes(a) > bytes(c); });
+    const int nc = n < kMaxChains ? n : kMaxChains;
+    b->chain_of.assign(nc, {});
+    for (int k = 0; k < n; ++k) b->chain_of[k % nc].push_back(order[k]);
+    b->cstream.assign(nc, nullptr);
+    b->cjoin.assign(nc, nullptr);
+    for (int c = 0; c < nc; ++c) {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->cstream[c], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->cjoin[c], cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Per-instance driver: nsteps steps of every instance, each by lbm_step on
+// its chain's stream (the instance's own 64-step graph replays, eager steps
+// outside them), the chains forked from and joined back to b->stream.
+int batch_step_instances(lbm_batch_ctx* b, int64_t nsteps)
+{
+    LBM_CUDA(batch_ensure_chains(b), "batch chain streams");
+    LBM_CUDA(cudaEventRecord(b->vfork, b->stream), "batch fork");
+    for (size_t c = 0; c < b->chain_of.size(); ++c) {
+        LBM_CUDA(cudaStreamWaitEvent(b->cstream[c], b->vfork, 0), "batch fork wait");
+        for (int i : b->chain_of[c]) {
+            lbm_ctx* h = b->inst[i];
+            h->stream = b->cstream[c];
+            const int rc = lbm_step(h, nsteps);
+            h->stream = b->stream;
+            if (rc) return rc;
+        }
+        LBM_CUDA(cudaEventRecord(b->cjoin[c], b->cstream[c]), "batch join");
+        LBM_CUDA(cudaStreamWaitEvent(b->stream, b->cjoin[c], 0), "batch join wait");
+    }
+    return LBM_OK;
 }
 
 // Records `steps` steps (from the natural layout) into the capture running on
@@ -1492,8 +1545,10 @@ int lbm_batch_set_stream(lbm_batch b, void* stream)
 int lbm_batch_set_mode(lbm_batch b, int mode, int steps_per_launch)
 {
     if (!b) return fail(LBM_EINVAL, "null batch");
-    if (mode != LBM_BATCH_PERSISTENT && mode != LBM_BATCH_PER_STEP) return fail(LBM_EINVAL, "unknown mode %d", mode);
+    if (mode != LBM_BATCH_PERSISTENT && mode != LBM_BATCH_PER_STEP && mode != LBM_BATCH_INSTANCES)
+        return fail(LBM_EINVAL, "unknown mode %d", mode);
     if (steps_per_launch < 1) return fail(LBM_EINVAL, "steps per launch must be >= 1");
+    if (mode != b->mode) batch_drop_graph(b);   // the graph holds one driver's launches
     b->mode = mode;
     b->chunk = steps_per_launch;
     return LBM_OK;
@@ -1516,7 +1571,7 @@ int lbm_batch_get_config(lbm_batch b, int* bx, int* by, int* mode, int* grid)
     if (bx) *bx = b->bx;
     if (by) *by = b->by;
     if (mode) *mode = b->mode;
-    if (grid) *grid = b->mode == LBM_BATCH_PERSISTENT ? b->persistent_grid : (int)b->ntiles;
+    if (grid) *grid = b->mode == LBM_BATCH_PERSISTENT ? b->persistent_grid : (int)b->ntiles;   // tiles: also per instance
     return LBM_OK;
 }
 
@@ -1539,6 +1594,18 @@ int lbm_batch_step(lbm_batch b, int64_t nsteps)
     if (rc) return rc;
     if (nsteps < 0) return fail(LBM_EINVAL, "negative step count");
     if (!b->initialized) return fail(LBM_ESTATE, "batch step before initialisation");
+    if (b->mode == LBM_BATCH_INSTANCES && nsteps > 0) {
+        // no stream: every instance in turn on the legacy stream
+        if (b->stream == nullptr) {
+            for (lbm_ctx* h : b->inst)
+                if ((rc = lbm_step(h, nsteps))) return rc;
+        } else if ((rc = batch_step_instances(b, nsteps))) {
+            return rc;
+        }
+        b->odd ^= (int)(nsteps & 1);
+        b->step += nsteps;
+        nsteps = 0;
+    }
     while (nsteps > 0) {
         if (b->mode == LBM_BATCH_PERSISTENT) {
             const int k = (int)(nsteps < b->chunk ? nsteps : b->chunk);
@@ -1655,6 +1722,33 @@ int lbm_batch_autotune(lbm_batch b, int reps, double* best_ms_per_step)
         }
         if (rc) break;
     }
+    if (rc == LBM_OK) {
+        // per-instance driver: every instance's own launch shape, then whole
+        // 64-step graphs of all chains
+        batch_sync_instances(b);
+        for (lbm_ctx* h : b->inst)
+            if ((rc = lbm_autotune(h, reps, nullptr))) break;
+        b->mode = LBM_BATCH_INSTANCES;
+        batch_drop_graph(b);
+        if (rc == LBM_OK) rc = lbm_batch_step(b, kBatchGraphSteps);   // warm-up, builds the graph
+        if (rc == LBM_OK) {
+            cudaEventRecord(e0, b->stream);
+            rc = lbm_batch_step(b, kBatchGraphSteps * (int64_t)reps);
+            cudaEventRecord(e1, b->stream);
+        }
+        if (rc == LBM_OK) rc = lbm_batch_synchronize(b);
+        if (rc == LBM_OK) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double per = ms / (double)(kBatchGraphSteps * reps);
+            if (per < best) {
+                best = per;
+                bbx = b->bx;
+                bby = b->by;
+                bmode = LBM_BATCH_INSTANCES;
+            }
+        }
+    }
     for (size_t i = 0; i < b->inst.size(); ++i) {
         cudaMemcpyAsync(b->inst[i]->store, backup[i], b->inst[i]->store_bytes, cudaMemcpyDeviceToDevice, b->stream);
     }
@@ -1703,6 +1797,10 @@ int lbm_batch_destroy(lbm_batch b)
         if (b->vjoin[v]) cudaEventDestroy(b->vjoin[v]);
     }
     if (b->vfork) cudaEventDestroy(b->vfork);
+    for (cudaStream_t cs : b->cstream)
+        if (cs) cudaStreamDestroy(cs);
+    for (cudaEvent_t ce : b->cjoin)
+        if (ce) cudaEventDestroy(ce);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return LBM_OK;

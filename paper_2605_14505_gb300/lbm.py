@@ -126,7 +126,7 @@ _SIGS = {
     "lbm_batch_set_barrier_test": ([_H, ctypes.c_uint, ctypes.c_uint], ctypes.c_int),
     "lbm_batch_destroy": ([_H], ctypes.c_int),
 }
-BATCH_MODES = {"persistent": 0, "per_step": 1}
+BATCH_MODES = {"persistent": 0, "per_step": 1, "instances": 2}
 
 _lib = None
 

@@ -1,5 +1,5 @@
-"""Batched instances (one launch for many lattices) against single-lattice runs
-and the oracle, both drivers, the 64-instance sweep, and the bounded grid
+"""Batched instances (many lattices advanced together) against single-lattice
+runs and the oracle, all three drivers, the 64-instance sweep, and the bounded grid
 barrier's timeout path (made to run out on purpose, with a short poll limit:
 the kernel returns an error status and the context stays usable)."""
 import numpy as np
@@ -72,6 +72,34 @@ def test_persistent_and_per_step_drivers_agree_bitwise():
         assert np.array_equal(fa, fc) and np.array_equal(ga, gc), i
     lbm.lbm_batch_destroy(a)
     lbm.lbm_batch_destroy(c)
+
+
+def test_instance_driver_is_the_single_lattice_run():
+    """The per-instance driver runs every instance's own single-lattice step
+    kernel (one graph branch per instance): bit for bit the solo run, through
+    two 64-step graph replays and an eager tail."""
+    b = _batch(SMALL, "instances")
+    lbm.lbm_batch_step(b, 131)
+    lbm.lbm_batch_synchronize(b)
+    assert lbm.lbm_batch_get_config(b)["mode"] == 2
+    for i, s in enumerate(SMALL):
+        p = _params(*s)
+        solo = lbm.Simulation(p)
+        solo.init_tgv(seed=5, noise_amp=0.02)
+        solo.step(131)
+        fs, gs = solo.populations()
+        fb, gb = _pops(lbm.lbm_batch_instance(b, i), p)
+        assert np.array_equal(fb, fs) and np.array_equal(gb, gs), i
+        assert lbm.lbm_step_count(lbm.lbm_batch_instance(b, i)) == 131
+        solo.close()
+    # switching drivers mid-run keeps the state (the graph is rebuilt)
+    lbm.lbm_batch_set_mode(b, "per_step")
+    lbm.lbm_batch_step(b, 64)
+    lbm.lbm_batch_set_mode(b, "instances")
+    lbm.lbm_batch_step(b, 64)
+    lbm.lbm_batch_synchronize(b)
+    assert all(np.isfinite(d["Ek"]) and d["step"] == 259 for d in lbm.lbm_batch_diagnostics(b))
+    lbm.lbm_batch_destroy(b)
 
 
 def test_batch_instance_against_oracle():
