@@ -359,7 +359,8 @@ def run_batch_sweep(args, peak):
     lbm.lbm_batch_step(b, 100)
     lbm.lbm_batch_synchronize(b)
     t = time.perf_counter()
-    lbm.lbm_batch_step(b, SWEEP_STEPS)
+    steps = args.sweep_steps
+    lbm.lbm_batch_step(b, steps)
     lbm.lbm_batch_synchronize(b)
     secs = time.perf_counter() - t
     nodes = sum(n ** 3 for n, *_ in specs)
@@ -368,9 +369,9 @@ def run_batch_sweep(args, peak):
     diags = lbm.lbm_batch_diagnostics(b)
     lbm.lbm_batch_destroy(b)
     torch.cuda.synchronize()
-    achieved = nbytes * SWEEP_STEPS / secs / 1e9
-    return {"instances": len(specs), "nodes": nodes, "steps": SWEEP_STEPS,
-            "mlups": round(nodes * SWEEP_STEPS / secs / 1e6, 1), "ms_per_step": round(secs * 1e3 / SWEEP_STEPS, 4),
+    achieved = nbytes * steps / secs / 1e9
+    return {"instances": len(specs), "nodes": nodes, "steps": steps,
+            "mlups": round(nodes * steps / secs / 1e6, 1), "ms_per_step": round(secs * 1e3 / steps, 4),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "bytes_per_step": nbytes},
             **({"driver": "instances", "launch_shapes": "per instance (autotuned)"} if cfg["mode"] == 2 else
@@ -379,7 +380,7 @@ def run_batch_sweep(args, peak):
             "autotune_ms_per_step": round(tuned_ms, 4),
             "l2": "achieved counts algorithmic bytes; the per-instance driver runs each instance's steps back "
                   "to back, so the 32^3-48^3 instances (12-40 MB) are partly served from L2 between steps",
-            "all_finite": all(np.isfinite(d["Ek"]) for d in diags), "timing": "host wall clock around 2000 steps"}
+            "all_finite": all(np.isfinite(d["Ek"]) for d in diags), "timing": f"host wall clock around {steps} steps"}
 
 
 def cpu_baseline(steps: int = 2) -> dict:
@@ -490,6 +491,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched sweep")
+    ap.add_argument("--sweep-steps", type=int, default=SWEEP_STEPS,
+                    help="timed steps of the batched sweep (fewer for a bounded profiler launch list)")
     ap.add_argument("--ncu-case", choices=["fp32", "fp16", "bf16", "19x7", "19x7-fp16", "batch", "batch-step"],
                     default=None,
                     help="run a small profiling case instead of the benchmark")
