@@ -623,6 +623,28 @@ __device__ __forceinline__ void eq_dev(float rho_m1, float rho, float ux, float 
     });
 }
 
+// IEEE 754 binary64 -> binary32 conversion, round to nearest, ties to even,
+// on the integer pipes: this GPU's FP64 pipe runs at a small fraction of its
+// FP32 rate, and with the hardware conversion (seven per node) the field
+// initialisation was bound by it. The float keeps the double's sign, its
+// exponent rebiased (1023 -> 127) and the top 23 of its 52 fraction bits; the
+// 29 bits below decide the rounding, and a carry out of the fraction moves
+// into the exponent (up to infinity) as IEEE rounding does. Zero is copied;
+// doubles whose float is subnormal or out of range, infinities and NaNs take
+// the hardware conversion.
+__device__ __forceinline__ float d2f_rn(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    if ((b << 1) == 0ull) return __uint_as_float(hi & 0x80000000u);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    if (e < 1 || e > 254) return __double2float_rn(v);
+    uint32_t r = (hi & 0x80000000u) | ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const uint32_t rest = lo & 0x1fffffffu;
+    if (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) ++r;
+    return __uint_as_float(r);
+}
+
 template <class L>
 __device__ __forceinline__ int canon_code(int i)
 {
@@ -640,22 +662,23 @@ __global__ void k_init_fields(InitArgs a)
         const double ux = a.u[idx], uy = a.u[n3 + idx], uz = a.u[2 * (size_t)n3 + idx];
         const double rp = a.rho_p[idx];
         float hf[P::QF], hg[P::QG];
-        eq_dev<LF>((float)(rho - 1.0), (float)rho, (float)ux, (float)uy, (float)uz, hf);
+        const float uxf = d2f_rn(ux), uyf = d2f_rn(uy), uzf = d2f_rn(uz);
+        eq_dev<LF>(d2f_rn(rho - 1.0), d2f_rn(rho), uxf, uyf, uzf, hf);
         // g_eq - w rho0 = w (rho' + (rho' + rho0) P)
-        eq_dev<LG>((float)rp, (float)(rp + a.rho0), (float)ux, (float)uy, (float)uz, hg);
+        eq_dev<LG>(d2f_rn(rp), d2f_rn(rp + a.rho0), uxf, uyf, uzf, hg);
         T* f = static_cast<T*>(a.f);
         T* g = static_cast<T*>(a.g);
         const uint32_t sidx = store_index_t<T>(a.geo, idx);
         sfor<0, P::QF>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             float v = hf[i];
-            if (a.xi_f) v += a.amp_f * LF::w(i) * (float)a.xi_f[(size_t)canon_code<LF>(i) * n3 + idx];
+            if (a.xi_f) v += a.amp_f * LF::w(i) * d2f_rn(a.xi_f[(size_t)canon_code<LF>(i) * n3 + idx]);
             st_pop<T>(f + (size_t)i * n3 + sidx, v);
         });
         sfor<0, P::QG>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             float v = hg[i];
-            if (a.xi_g) v += a.amp_f * LG::w(i) * (float)a.xi_g[(size_t)canon_code<LG>(i) * n3 + idx];
+            if (a.xi_g) v += a.amp_f * LG::w(i) * d2f_rn(a.xi_g[(size_t)canon_code<LG>(i) * n3 + idx]);
             st_pop<T>(g + (size_t)i * n3 + sidx, v);
         });
     }

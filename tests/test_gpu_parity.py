@@ -470,3 +470,57 @@ def test_store_row_order(storage, nx):
     assert np.max(np.abs(f - wf[:, None] - code_f)) < 1e-12
     assert np.max(np.abs(g - p.rho0 * wg[:, None] - code_g)) < 1e-12
     s.close()
+
+
+def test_field_initialisation_rounds_fp64_fields_to_nearest_even():
+    """lbm_init_fields rounds the FP64 host fields to FP32 as IEEE 754 does
+    (to nearest, ties to even) before the FP32 equilibria. With u = 0 the
+    rest slots hold w_0 float(rho - 1) and w_0^g (float(rho') + 0); with rho = 1 and
+    u = (u_x, 0, 0) the f rest slot holds w_0 (-(3/2) float(u_x)^2). Fed
+    random values, exact ties between adjacent floats (both parities of the
+    lower one), values that round up into the next binade, float-subnormal
+    and double-subnormal values and zeros of both signs, the FP32 store must
+    equal numpy's float32 rounding bit for bit."""
+    import torch
+
+    rng = np.random.default_rng(3)
+    anchors = rng.uniform(-0.3, 0.3, 400).astype(np.float32)
+    nxt = np.nextafter(anchors, np.float32(np.inf))
+    ties = (anchors.astype(np.float64) + nxt.astype(np.float64)) / 2.0
+    rand = rng.uniform(-1.0, 1.0, 400) * 10.0 ** rng.integers(-30, 3, 400).astype(np.float64)
+    up = np.ldexp(2.0 - 2.0 ** -30, rng.integers(-40, -2, 100)) * rng.choice([-1.0, 1.0], 100)
+    tiny = np.array([1e-40, -3e-42, 5e-324, -2.5e-310, 1e-45, 7e-46, 1.4e-45, 0.0, -0.0])
+    vals = np.concatenate([ties, rand, up, tiny])
+    nx, ny, nz = 64, 16, 4
+    n3 = nx * ny * nz
+    k = len(vals)
+    assert 3 * k <= n3
+    rho = np.ones(n3)
+    u = np.zeros(3 * n3)
+    rp = np.zeros(n3)
+    # rho - 1 path: ties and values in the range where 1 + t is exact
+    drho = np.concatenate([ties, rng.uniform(-0.3, 0.3, k - len(ties))])
+    rho[:k] = 1.0 + drho
+    # u_x path: values whose FP32 square stays normal (a square that underflows
+    # to zero says nothing about the conversion)
+    rand_u = np.where(np.abs(rand) < 1e-18, 0.1, rand)
+    u[k:2 * k] = np.concatenate([ties, rand_u, up, np.full(len(tiny), 0.25)])
+    rp[2 * k:3 * k] = vals
+    p = lattice_params(nx, ny, nz, "27x19", "sc", 0.55, 0.6, 0.0, 0.0)
+    s = gpu_sim(p, "fp32")
+    s.init_fields(rho, u, rp)
+    s.synchronize()
+    raw = s._store.view(torch.float32).cpu().numpy()
+    f0, g0 = raw[:n3], raw[27 * n3: 28 * n3]   # rest slots (slot 0 of f and of g)
+    w0 = np.float32(8.0 / 27.0)
+    w0g = np.float32(1.0 / 3.0)
+    with np.errstate(over="ignore", under="ignore"):
+        exp_rho = w0 * (rho[:k] - 1.0).astype(np.float32)
+        uxf = u[k:2 * k].astype(np.float32)
+        exp_u = w0 * (np.float32(-1.5) * (uxf * uxf))
+        # the FMA adds the (zero) equilibrium term: -0 + 0 = +0, as IEEE rounds
+        exp_rp = w0g * (rp[2 * k:3 * k].astype(np.float32) + np.float32(0.0))
+    assert np.array_equal(f0[:k].view(np.uint32), exp_rho.view(np.uint32))
+    assert np.array_equal(f0[k:2 * k].view(np.uint32), exp_u.view(np.uint32))
+    assert np.array_equal(g0[2 * k:3 * k].view(np.uint32), exp_rp.view(np.uint32))
+    s.close()
