@@ -284,11 +284,11 @@ int lbm_get_block(lbm_handle h, int* bx, int* by);
  * so the simulation is unchanged. best_ms_per_step may be NULL. */
 int lbm_autotune(lbm_handle h, int reps, double* best_ms_per_step);
 
-/* For FP16/BF16 storage and even nx the step kernel can update two
- * x-adjacent nodes per thread, moving each pair's values of a slot as one
- * 32-bit word where the AA access keeps them aligned (every slot of the even
- * step; on the odd step, whose pairs are (x0 - 1, x0), the slots with
- * e_x != 0); the per-node arithmetic is the one-node kernel's.
+/* For FP16/BF16 storage and even nx the step kernel can update two nodes
+ * per thread: nodes k and k + nx/2 of a row, which the half-row order of the
+ * store (see lbm_attach) keeps in one 32-bit word, so that every slot of
+ * both AA steps moves as one aligned word; the per-node arithmetic is the
+ * one-node kernel's.
  * mode: LBM_PAIRING_OFF (one node per thread), LBM_PAIRING_ALL (the default:
  * two nodes per thread at both AA parities), LBM_PAIRING_EVEN (two nodes on
  * even steps, one node on odd steps).
