@@ -275,13 +275,18 @@ int lbm_diagnostics_noalloc(lbm_handle h, lbm_diag* out);
 
 /* Launch shape of the step kernel (threads along x and y; bx * by <= 256,
  * bx a multiple of 32). With two nodes per thread (lbm_set_pairing) a
- * thread along x covers two nodes. */
+ * thread along x covers two nodes. Each AA parity has its own shape:
+ * lbm_set_block sets both, lbm_get_block returns the even steps' shape (the
+ * default odd-step shape of the D3Q27xD3Q19 two-nodes-per-thread kernel
+ * with FP16 storage is one row of 128 threads, its even-step shape 64 x 2). */
 int lbm_set_block(lbm_handle h, int bx, int by);
 int lbm_get_block(lbm_handle h, int* bx, int* by);
 
 /* Time each candidate launch shape on this lattice (reps even+odd step pairs
- * each, CUDA events) and keep the fastest. The state is saved and restored,
- * so the simulation is unchanged. best_ms_per_step may be NULL. */
+ * each, every launch timed on its own with CUDA events) and keep the fastest
+ * for each AA parity. The state is saved and restored, so the simulation is
+ * unchanged. best_ms_per_step (the mean of the two parities' best) may be
+ * NULL. */
 int lbm_autotune(lbm_handle h, int reps, double* best_ms_per_step);
 
 /* For FP16/BF16 storage and even nx the step kernel can update two nodes

@@ -82,7 +82,8 @@ struct lbm_ctx {
     bool initialized = false;
     int64_t step = 0;
     int odd = 0;           // layout parity of the store
-    int bx = 0, by = 0;
+    int bx = 0, by = 0;      // launch shape of the even AA steps
+    int bxo = 0, byo = 0;    // and of the odd ones
     int pairing = LBM_PAIRING_ALL;   // two nodes per thread (16-bit storage, even nx)
     bool tile_staging = false;        // bulk-copy staged kernel where it applies
     int stage_grid = 0;               // persistent grid of the staged kernel (0: not derived yet)
@@ -157,22 +158,35 @@ bool uses_pairs(const lbm_ctx* h, int odd)
     return wanted && h->ks->step2[h->p.forcing][0] != nullptr && (h->p.nx % 2) == 0;
 }
 
-// Default launch shape, from a sweep of the candidate shapes at 256^3: the
-// two-nodes-per-thread kernel runs best in 128-thread blocks of 64 x 2 (four
-// 128-register blocks per SM), the one-node kernels in blocks of one row of
-// 256 threads for D3Q27xD3Q19 and 128 for the smaller pairs.
+// Default launch shape of one AA parity, from sweeps of the candidate shapes
+// at 256^3: the two-nodes-per-thread kernel runs best in 128-thread blocks
+// (four 128-register blocks per SM), of 64 x 2, except on the odd steps of
+// D3Q27xD3Q19 with FP16 storage, where one row of 128 is faster (0.488
+// against 0.492 ms; with BF16 it is slower); the one-node kernels in blocks
+// of one row of 256 threads for D3Q27xD3Q19 and 128 for the smaller pairs,
+// at either parity.
+void pick_block(const lbm_ctx* h, int odd, int& bx, int& by)
+{
+    const bool pairs = uses_pairs(h, odd);
+    const int xunits = pairs ? h->p.nx / 2 : h->p.nx;
+    const bool big = h->q.qf + h->q.qg >= 46;
+    const int threads = pairs ? 128 : (big ? 256 : 128);
+    const int want = pairs ? ((odd && big && h->p.storage == LBM_FP16_DEV) ? 128 : 64) : threads;
+    bx = 32;
+    while (bx * 2 <= want && bx * 2 <= xunits) bx *= 2;
+    by = threads / bx;
+    while (by > 1 && by / 2 >= h->p.ny) by /= 2;
+}
+
 void default_block(lbm_ctx* h)
 {
-    const bool pairs = uses_pairs(h, 0);
-    const int xunits = pairs ? h->p.nx / 2 : h->p.nx;
-    const int threads = pairs ? 128 : (h->q.qf + h->q.qg >= 46 ? 256 : 128);
-    const int want = pairs ? 64 : threads;
-    int bx = 32;
-    while (bx * 2 <= want && bx * 2 <= xunits) bx *= 2;
-    int by = threads / bx;
-    while (by > 1 && by / 2 >= h->p.ny) by /= 2;
-    h->bx = bx;
-    h->by = by;
+    pick_block(h, 0, h->bx, h->by);
+    pick_block(h, 1, h->bxo, h->byo);
+}
+
+dim3 step_block(const lbm_ctx* h, int odd)
+{
+    return odd ? dim3((unsigned)h->bxo, (unsigned)h->byo) : dim3((unsigned)h->bx, (unsigned)h->by);
 }
 
 void drop_graph(lbm_ctx* h)
@@ -304,7 +318,8 @@ int fill_diag(const lbm_ctx* h, int64_t step, lbm_diag* out)
 dim3 step_grid(const lbm_ctx* h, int odd)
 {
     const int xunits = uses_pairs(h, odd) ? h->p.nx / 2 : h->p.nx;
-    return dim3((unsigned)((xunits + h->bx - 1) / h->bx), (unsigned)((h->p.ny + h->by - 1) / h->by),
+    const dim3 b = step_block(h, odd);
+    return dim3((unsigned)((xunits + (int)b.x - 1) / (int)b.x), (unsigned)((h->p.ny + (int)b.y - 1) / (int)b.y),
                 (unsigned)h->p.nz);
 }
 
@@ -349,7 +364,7 @@ cudaError_t launch_step(lbm_ctx* h, int odd, cudaStream_t s)
     a.ph = h->ph;
     void* args[] = {&a};
     const void* k = uses_pairs(h, odd) ? h->ks->step2[h->p.forcing][odd] : h->ks->step[h->p.forcing][odd];
-    return cudaLaunchKernel(k, step_grid(h, odd), dim3(h->bx, h->by), args, 0, s);
+    return cudaLaunchKernel(k, step_grid(h, odd), step_block(h, odd), args, 0, s);
 }
 
 int flat_grid(const lbm_ctx* h)
@@ -817,7 +832,7 @@ int lbm_step_diagnostics(lbm_handle h, int64_t nsteps, lbm_diag* out)
     a.dg = DiagSink{da.ep_scale, da.epsk_scale, da.s_scale, h->diag_fields, h->diag_partials};
     void* args[] = {&a};
     const void* k = pairs ? h->ks->step2_diag[h->p.forcing][odd] : h->ks->step_diag[h->p.forcing][odd];
-    LBM_CUDA(cudaLaunchKernel(k, grid, dim3(h->bx, h->by), args, 0, h->stream), "diagnosing step");
+    LBM_CUDA(cudaLaunchKernel(k, grid, step_block(h, odd), args, 0, h->stream), "diagnosing step");
     const int64_t step0 = h->step;
     h->odd ^= 1;
     h->step += 1;
@@ -977,8 +992,8 @@ int lbm_set_block(lbm_handle h, int bx, int by)
     if (!h) return fail(LBM_EINVAL, "null handle");
     if (bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 256)
         return fail(LBM_EINVAL, "block (%d, %d): bx must be a positive multiple of 32 and bx*by <= 256", bx, by);
-    h->bx = bx;
-    h->by = by;
+    h->bx = h->bxo = bx;
+    h->by = h->byo = by;
     drop_graph(h);
     return LBM_OK;
 }
@@ -1002,51 +1017,61 @@ int lbm_autotune(lbm_handle h, int reps, double* best_ms_per_step)
     void* backup = nullptr;
     size_t bytes = (size_t)(h->q.qf + h->q.qg) * h->geo.n3 * elem_size(h->p.storage);
     LBM_CUDA(cudaMalloc(&backup, bytes), "autotune backup allocation");
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    // one event between consecutive launches, so that each launch is timed
+    // on its own and the two AA parities get their own best shape
+    std::vector<cudaEvent_t> ev(2 * (size_t)reps + 1, nullptr);
+    for (cudaEvent_t& e : ev) cudaEventCreate(&e);
     cudaMemcpyAsync(backup, h->store, bytes, cudaMemcpyDeviceToDevice, h->stream);
-    const int save_bx = h->bx, save_by = h->by, save_odd = h->odd;
-    double best = 1e300;
-    int bbx = save_bx, bby = save_by;
+    const int save_bx = h->bx, save_by = h->by, save_bxo = h->bxo, save_byo = h->byo, save_odd = h->odd;
+    double best[2] = {1e300, 1e300};
+    int bbx[2] = {save_bx, save_bxo}, bby[2] = {save_by, save_byo};
     cudaError_t err = cudaSuccess;
     for (const auto& c : cand) {
         if (c[0] > 32 && c[0] / 2 >= h->p.nx) continue;  // wider than the row
         if (c[1] > 1 && (c[1] / 2) >= h->p.ny) continue;
-        h->bx = c[0];
-        h->by = c[1];
+        h->bx = h->bxo = c[0];
+        h->by = h->byo = c[1];
         // warm-up pair, then timed pairs
         for (int s = 0; s < 2 && err == cudaSuccess; ++s) err = launch_step(h, (save_odd + s) & 1, h->stream);
-        cudaEventRecord(e0, h->stream);
-        for (int s = 0; s < 2 * reps && err == cudaSuccess; ++s) err = launch_step(h, (save_odd + s) & 1, h->stream);
-        cudaEventRecord(e1, h->stream);
-        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-        if (err != cudaSuccess) break;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        double per = ms / (2.0 * reps);
-        if (per < best) {
-            best = per;
-            bbx = c[0];
-            bby = c[1];
+        if (err == cudaSuccess) err = cudaEventRecord(ev[0], h->stream);
+        for (int s = 0; s < 2 * reps && err == cudaSuccess; ++s) {
+            err = launch_step(h, (save_odd + s) & 1, h->stream);
+            if (err == cudaSuccess) err = cudaEventRecord(ev[s + 1], h->stream);
         }
+        if (err == cudaSuccess) err = cudaEventSynchronize(ev[2 * reps]);
+        if (err != cudaSuccess) break;
+        double t[2] = {0.0, 0.0};
+        for (int s = 0; s < 2 * reps; ++s) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[s], ev[s + 1]);
+            t[(save_odd + s) & 1] += ms / reps;
+        }
+        for (int par = 0; par < 2; ++par)
+            if (t[par] < best[par]) {
+                best[par] = t[par];
+                bbx[par] = c[0];
+                bby[par] = c[1];
+            }
     }
     cudaMemcpyAsync(h->store, backup, bytes, cudaMemcpyDeviceToDevice, h->stream);
     cudaError_t e2 = cudaStreamSynchronize(h->stream);
     cudaFree(backup);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
     h->odd = save_odd;
     if (err != cudaSuccess) {
         h->bx = save_bx;
         h->by = save_by;
+        h->bxo = save_bxo;
+        h->byo = save_byo;
         return cuda_fail(err, "autotune");
     }
     if (e2 != cudaSuccess) return cuda_fail(e2, "autotune restore");
-    h->bx = bbx;
-    h->by = bby;
+    h->bx = bbx[0];
+    h->by = bby[0];
+    h->bxo = bbx[1];
+    h->byo = bby[1];
     drop_graph(h);
-    if (best_ms_per_step) *best_ms_per_step = best;
+    if (best_ms_per_step) *best_ms_per_step = 0.5 * (best[0] + best[1]);
     return LBM_OK;
 }
 

@@ -355,20 +355,23 @@ struct PairAddr {
 };
 
 // The seam lanes of a pair: k = 0 (first) and k = half - 1 (last), and
-// whether any lane of the warp is one (a warp-uniform branch condition).
+// whether any lane of the warp is one (a warp-uniform branch condition). In
+// those warps every lane permutes the seam slots' words with its own
+// selector: the halves exchanged on a seam lane, unchanged elsewhere.
 struct Seam {
     bool first, last, warp_first, warp_last;
+    uint32_t sel_first, sel_last;   // byte-permute selectors: exchange halves on the seam lanes
     __device__ __forceinline__ Seam(const Geometry& g, int x0)
     {
         first = x0 == 0;
         last = x0 == g.nx - 2;
+        sel_first = first ? 0x1032u : 0x3210u;
+        sel_last = last ? 0x1032u : 0x3210u;
         const unsigned m = __activemask();
         warp_first = __any_sync(m, first);
         warp_last = __any_sync(m, last);
     }
 };
-
-__device__ __forceinline__ uint32_t swap_halves(uint32_t w) { return __byte_perm(w, 0u, 0x1032); }
 
 // Loads default-cached: the odd step writes each word back shortly after
 // reading it, and a word still in L2 takes the write without a miss.
@@ -400,13 +403,13 @@ __device__ __forceinline__ void load_pair(const unsigned short* __restrict__ b16
         if (sm.warp_first) {
             sfor<0, L::kQ>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                if constexpr (L::ex(i) == 1) w[i] = sm.first ? swap_halves(w[i]) : w[i];
+                if constexpr (L::ex(i) == 1) w[i] = __byte_perm(w[i], 0u, sm.sel_first);
             });
         }
         if (sm.warp_last) {
             sfor<0, L::kQ>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                if constexpr (L::ex(i) == -1) w[i] = sm.last ? swap_halves(w[i]) : w[i];
+                if constexpr (L::ex(i) == -1) w[i] = __byte_perm(w[i], 0u, sm.sel_last);
             });
         }
     }
@@ -420,13 +423,13 @@ __device__ __forceinline__ void store_pair(unsigned short* __restrict__ b16, uin
         if (sm.warp_first) {
             sfor<0, L::kQ>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                if constexpr (L::ex(i) == -1) w[i] = sm.first ? swap_halves(w[i]) : w[i];
+                if constexpr (L::ex(i) == -1) w[i] = __byte_perm(w[i], 0u, sm.sel_first);
             });
         }
         if (sm.warp_last) {
             sfor<0, L::kQ>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                if constexpr (L::ex(i) == 1) w[i] = sm.last ? swap_halves(w[i]) : w[i];
+                if constexpr (L::ex(i) == 1) w[i] = __byte_perm(w[i], 0u, sm.sel_last);
             });
         }
     }

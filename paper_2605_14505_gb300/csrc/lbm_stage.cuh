@@ -181,13 +181,13 @@ __device__ __forceinline__ void stage_load(const uint16_t* rows, int RS, int p, 
         if (sm.warp_first) {
             sfor<0, L::kQ>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                if constexpr (L::ex(i) == 1) w[i] = sm.first ? swap_halves(w[i]) : w[i];
+                if constexpr (L::ex(i) == 1) w[i] = __byte_perm(w[i], 0u, sm.sel_first);
             });
         }
         if (sm.warp_last) {
             sfor<0, L::kQ>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                if constexpr (L::ex(i) == -1) w[i] = sm.last ? swap_halves(w[i]) : w[i];
+                if constexpr (L::ex(i) == -1) w[i] = __byte_perm(w[i], 0u, sm.sel_last);
             });
         }
     }
