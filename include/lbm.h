@@ -277,8 +277,8 @@ int lbm_diagnostics_noalloc(lbm_handle h, lbm_diag* out);
  * bx a multiple of 32). With two nodes per thread (lbm_set_pairing) a
  * thread along x covers two nodes. Each AA parity has its own shape:
  * lbm_set_block sets both, lbm_get_block returns the even steps' shape (the
- * default odd-step shape of the D3Q27xD3Q19 two-nodes-per-thread kernel
- * with FP16 storage is one row of 128 threads, its even-step shape 64 x 2). */
+ * default odd-step shape of the D3Q27xD3Q19 two-nodes-per-thread kernel is
+ * one row of 128 threads, its even-step shape 64 x 2). */
 int lbm_set_block(lbm_handle h, int bx, int by);
 int lbm_get_block(lbm_handle h, int* bx, int* by);
 

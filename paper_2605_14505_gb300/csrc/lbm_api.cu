@@ -158,20 +158,19 @@ bool uses_pairs(const lbm_ctx* h, int odd)
     return wanted && h->ks->step2[h->p.forcing][0] != nullptr && (h->p.nx % 2) == 0;
 }
 
-// Default launch shape of one AA parity, from sweeps of the candidate shapes
-// at 256^3: the two-nodes-per-thread kernel runs best in 128-thread blocks
-// (four 128-register blocks per SM), of 64 x 2, except on the odd steps of
-// D3Q27xD3Q19 with FP16 storage, where one row of 128 is faster (0.488
-// against 0.492 ms; with BF16 it is slower); the one-node kernels in blocks
-// of one row of 256 threads for D3Q27xD3Q19 and 128 for the smaller pairs,
-// at either parity.
+// Default launch shape of one AA parity, from per-parity sweeps of the
+// candidate shapes at 256^3: the two-nodes-per-thread kernel runs best in
+// 128-thread blocks of 64 x 2, except on the odd steps of D3Q27xD3Q19, where
+// one row of 128 is faster (FP16 0.462 against 0.465 ms, BF16 0.462 against
+// 0.467 ms); the one-node kernels in blocks of one row of 256 threads for
+// D3Q27xD3Q19 and 128 for the smaller pairs, at either parity.
 void pick_block(const lbm_ctx* h, int odd, int& bx, int& by)
 {
     const bool pairs = uses_pairs(h, odd);
     const int xunits = pairs ? h->p.nx / 2 : h->p.nx;
     const bool big = h->q.qf + h->q.qg >= 46;
     const int threads = pairs ? 128 : (big ? 256 : 128);
-    const int want = pairs ? ((odd && big && h->p.storage == LBM_FP16_DEV) ? 128 : 64) : threads;
+    const int want = pairs ? ((odd && big) ? 128 : 64) : threads;
     bx = 32;
     while (bx * 2 <= want && bx * 2 <= xunits) bx *= 2;
     by = threads / bx;

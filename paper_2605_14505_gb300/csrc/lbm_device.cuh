@@ -380,21 +380,72 @@ LBM_HD float fast_div(float a, float b)
 #endif
 }
 
+// Moment sums of one node for the short forms (16-bit storage), accumulated
+// opposite pair by opposite pair, and the coupled solve. node_macro's short
+// path and the two-node word kernels share it, so both give the same bits.
+template <class P>
+struct FastMoments {
+    using LF = typename P::LF;
+    float drho, jx, jy, jz, a;
+    LBM_HD FastMoments(float h0, float k0) : drho(h0), jx(0.f), jy(0.f), jz(0.f), a(k0) {}
+    template <int I>
+    LBM_HD void f_pair(float hi, float hj)
+    {
+        const float sum = hi + hj;
+        const float dif = hi - hj;
+        drho += sum;
+        if constexpr (LF::ex(I) == 1) jx += dif;
+        if constexpr (LF::ex(I) == -1) jx -= dif;
+        if constexpr (LF::ey(I) == 1) jy += dif;
+        if constexpr (LF::ey(I) == -1) jy -= dif;
+        if constexpr (LF::ez(I) == 1) jz += dif;
+        if constexpr (LF::ez(I) == -1) jz -= dif;
+    }
+    template <int I>
+    LBM_HD void g_pair(float ki, float kj) { a += ki + kj; }
+    LBM_HD Macro solve(const Phys& ph) const
+    {
+        Macro m;
+        m.drho = drho;
+        m.jx = jx; m.jy = jy; m.jz = jz;
+        m.a = a;
+        m.rho = 1.f + drho;
+        m.irho = 1.f / m.rho;
+        m.dirho = m.irho - 1.f;
+        m.rho_p = fast_div(a + ph.kappa * jz * m.irho, 1.f + 0.5f * ph.kappa * ph.G * m.irho);
+        m.Fz = -ph.G * m.rho_p;
+        m.ux = jx * m.irho;
+        m.uy = jy * m.irho;
+        m.uz = (jz + 0.5f * m.Fz) * m.irho;
+        return m;
+    }
+};
+
 template <class P, bool EXACT = true>
 LBM_HD Macro node_macro(float* h, float* k, const Phys& ph)
 {
     using LF = typename P::LF;
     using LG = typename P::LG;
+    if constexpr (!EXACT) {
+        FastMoments<P> s(h[0], k[0]);
+        sfor<0, kPairs<LF>>([&](auto mc) {
+            constexpr int i = 2 * decltype(mc)::value + 1;
+            s.template f_pair<i>(h[i], h[i + 1]);
+        });
+        sfor<0, kPairs<LG>>([&](auto mc) {
+            constexpr int i = 2 * decltype(mc)::value + 1;
+            s.template g_pair<i>(k[i], k[i + 1]);
+        });
+        return s.solve(ph);
+    }
     Macro m;
     float drho = h[0], jx = 0.f, jy = 0.f, jz = 0.f, a = k[0];
     sfor<0, kPairs<LF>>([&](auto mc) {
         constexpr int i = 2 * decltype(mc)::value + 1;
         const float sum = h[i] + h[i + 1];
         const float dif = h[i] - h[i + 1];
-        if constexpr (EXACT) {
-            h[i] = sum;       // pair form, see collide_f
-            h[i + 1] = dif;
-        }
+        h[i] = sum;       // pair form, see collide_f
+        h[i + 1] = dif;
         drho += sum;
         if constexpr (LF::ex(i) == 1) jx += dif;
         if constexpr (LF::ex(i) == -1) jx -= dif;
@@ -406,26 +457,13 @@ LBM_HD Macro node_macro(float* h, float* k, const Phys& ph)
     sfor<0, kPairs<LG>>([&](auto mc) {
         constexpr int i = 2 * decltype(mc)::value + 1;
         const float sum = k[i] + k[i + 1];
-        if constexpr (EXACT) {
-            k[i + 1] = k[i] - k[i + 1];
-            k[i] = sum;
-        }
+        k[i + 1] = k[i] - k[i + 1];
+        k[i] = sum;
         a += sum;
     });
     m.drho = drho;
     m.jx = jx; m.jy = jy; m.jz = jz;
     m.a = a;
-    if constexpr (!EXACT) {
-        m.rho = 1.f + drho;
-        m.irho = 1.f / m.rho;
-        m.dirho = m.irho - 1.f;
-        m.rho_p = fast_div(a + ph.kappa * jz * m.irho, 1.f + 0.5f * ph.kappa * ph.G * m.irho);
-        m.Fz = -ph.G * m.rho_p;
-        m.ux = jx * m.irho;
-        m.uy = jy * m.irho;
-        m.uz = (jz + 0.5f * m.Fz) * m.irho;
-        return m;
-    }
     m.dirho = -drho / (1.f + drho);
     m.rho = 1.f + drho;
     m.irho = 1.f + m.dirho;
@@ -594,54 +632,69 @@ LBM_HD void collide_g(float* k, const Macro& m, const Phys& ph)
 // coefficient per weight class, and rho (e.u)^2 = (e.j)^2 / rho, so that each
 // opposite pair costs e.j, two multiplies, three FMAs and an add/subtract.
 // FP32 arithmetic still; its rounding is ~1e-7 of values stored to 2^-11
-// (FP16) or 2^-8 (BF16).
+// (FP16) or 2^-8 (BF16). FastF and FastG hold one node's coefficients and
+// update one opposite pair at a time: collide_f_fast / collide_g_fast apply
+// them to one node's array, the two-node kernels to both halves of each
+// packed 32-bit word.
 // ---------------------------------------------------------------------------
 template <class P, int FORCING>
-LBM_HD void collide_f_fast(float* h, const Macro& m, const Phys& ph)
-{
+struct FastF {
     using LF = typename P::LF;
-    constexpr float c1 = LF::inv_cs2, c2 = LF::half_inv_cs4, c0 = LF::half_inv_cs2;
-    const float om = 2.f - ph.delta_f;   // 1 / tau_f
-    const float cm = ph.delta_f - 1.f;   // 1 - 1 / tau_f
-    // momentum of the equilibrium velocity (as in collide_f)
-    float mx = m.jx, my = m.jy, mz;
-    if constexpr (FORCING == kGuo || FORCING == kHCZ) {
-        mz = m.jz + 0.5f * m.Fz;
-    } else if constexpr (FORCING == kShanChen) {
-        mz = m.jz + ph.sc_tau * m.Fz;
-    } else {
-        mz = m.jz;
-    }
-    const float mv = (mx * mx + my * my + mz * mz) * m.irho;       // rho |v|^2
-    float base = m.drho - c0 * mv;
-    // forcing (Eqs. 8-10 and the cited schemes); v = j_eq / rho
-    const float vz = mz * m.irho;
-    // Guo folded into the equilibrium as in collide_f: base - (tau - 1/2) F_z v_z / cs^2,
-    // e.j + 2 (tau - 1/2) F_z e_z in the even part, e.j + (tau - 1/2) F_z e_z in the odd part
-    const float gFo = (FORCING == kGuo) ? ph.guo_tau * m.Fz : 0.f;
-    if constexpr (FORCING == kGuo) base = fmaf(-gFo * c1, vz, base);
-    const float ob = om * base;               // omega (f_eq_i - w_i) / w_i without the e terms
-    const float o2 = om * c2 * m.irho;        // omega rho (e.v)^2 / (2 cs^4) per (e.j)^2
-    const float o1 = om * c1;                 // omega rho e.v / cs^2 per e.j
-    const float gF = ph.guo_pref * m.Fz;
-    const float du = m.Fz * m.irho;
-    const float dusq = du * (2.f * vz + du);
+    static constexpr float c1 = LF::inv_cs2, c2 = LF::half_inv_cs4, c0 = LF::half_inv_cs2;
+    float om, cm;               // 1 / tau_f, 1 - 1 / tau_f
+    float mx, my, mz;           // momentum of the equilibrium velocity (as in collide_f)
+    float mv, base, vz, gFo, ob, o2, o1, gF, du, dusq, irho, rho, Fz, drho;
+    LBM_HD FastF(const Macro& m, const Phys& ph)
     {
-        const float heq = LF::w(0) * base + LF::kMassCorr * m.drho + LF::kUsqCorr * mv;
+        om = 2.f - ph.delta_f;
+        cm = ph.delta_f - 1.f;
+        mx = m.jx;
+        my = m.jy;
+        if constexpr (FORCING == kGuo || FORCING == kHCZ) {
+            mz = m.jz + 0.5f * m.Fz;
+        } else if constexpr (FORCING == kShanChen) {
+            mz = m.jz + ph.sc_tau * m.Fz;
+        } else {
+            mz = m.jz;
+        }
+        mv = (mx * mx + my * my + mz * mz) * m.irho;       // rho |v|^2
+        base = m.drho - c0 * mv;
+        // forcing (Eqs. 8-10 and the cited schemes); v = j_eq / rho
+        vz = mz * m.irho;
+        // Guo folded into the equilibrium as in collide_f: base - (tau - 1/2) F_z v_z / cs^2,
+        // e.j + 2 (tau - 1/2) F_z e_z in the even part, e.j + (tau - 1/2) F_z e_z in the odd part
+        gFo = (FORCING == kGuo) ? ph.guo_tau * m.Fz : 0.f;
+        if constexpr (FORCING == kGuo) base = fmaf(-gFo * c1, vz, base);
+        ob = om * base;               // omega (f_eq_i - w_i) / w_i without the e terms
+        o2 = om * c2 * m.irho;        // omega rho (e.v)^2 / (2 cs^4) per (e.j)^2
+        o1 = om * c1;                 // omega rho e.v / cs^2 per e.j
+        gF = ph.guo_pref * m.Fz;
+        du = m.Fz * m.irho;
+        dusq = du * (2.f * vz + du);
+        irho = m.irho;
+        rho = m.rho;
+        Fz = m.Fz;
+        drho = m.drho;
+    }
+    // the rest population
+    LBM_HD float rest(float h0) const
+    {
+        const float heq = LF::w(0) * base + LF::kMassCorr * drho + LF::kUsqCorr * mv;
         float F0 = 0.f;   // (Guo: folded into base)
         if constexpr (FORCING == kHCZ) {
-            const float vsq = mv * m.irho;
+            const float vsq = mv * irho;
             F0 = -gF * c1 * vz * LF::w(0) * (1.f - c0 * vsq);
         }
-        if constexpr (FORCING == kEDM) F0 = (-c0 * LF::w(0) + LF::kUsqCorr) * (m.rho * dusq);
-        h[0] = fmaf(cm, h[0], fmaf(om, heq, F0));
+        if constexpr (FORCING == kEDM) F0 = (-c0 * LF::w(0) + LF::kUsqCorr) * (rho * dusq);
+        return fmaf(cm, h0, fmaf(om, heq, F0));
     }
-    sfor<0, kPairs<LF>>([&](auto mc) {
-        constexpr int i = 2 * decltype(mc)::value + 1;
-        constexpr int j = i + 1;
-        constexpr float w = LF::w(i);
-        constexpr int ez = LF::ez(i);
-        const float em = e_dot<LF, i>(mx, my, mz);
+    // the opposite pair (I, I + 1), in place
+    template <int I>
+    LBM_HD void pair(float& hi, float& hj) const
+    {
+        constexpr float w = LF::w(I);
+        constexpr int ez = LF::ez(I);
+        const float em = e_dot<LF, I>(mx, my, mz);
         float emo = em;          // e.j of the odd part
         float hs;
         if constexpr (FORCING == kGuo && ez != 0) {
@@ -652,53 +705,83 @@ LBM_HD void collide_f_fast(float* h, const Macro& m, const Phys& ph)
         }
         float ha = 0.f;          // forcing part of the odd term; the equilibrium part is (w o1) e.j
         if constexpr (FORCING == kHCZ) {
-            const float eu = em * m.irho;
-            const float ps = 1.f + c2 * eu * eu - c0 * mv * m.irho;
+            const float eu = em * irho;
+            const float ps = 1.f + c2 * eu * eu - c0 * mv * irho;
             const float pa = c1 * eu;
             const float c = gF * c1 * w;
             hs += c * ((float)ez * pa - vz * ps);
             ha += c * ((float)ez * ps - vz * pa);
         } else if constexpr (FORCING == kEDM) {
             float ps = -c0 * dusq;
-            if constexpr (ez != 0) ps += c2 * du * (2.f * (float)ez * (em * m.irho) + du);
-            hs += w * m.rho * ps;
-            if constexpr (ez != 0) ha += w * c1 * (float)ez * m.Fz;
+            if constexpr (ez != 0) ps += c2 * du * (2.f * (float)ez * (em * irho) + du);
+            hs += w * rho * ps;
+            if constexpr (ez != 0) ha += w * c1 * (float)ez * Fz;
         }
         float hp = hs, hm = hs;
         if constexpr (FORCING == kHCZ || FORCING == kEDM) {
             hp = hs + ha;
             hm = hs - ha;
         }
-        h[i] = fmaf(cm, h[i], fmaf(w * o1, emo, hp));
-        h[j] = fmaf(cm, h[j], fmaf(-(w * o1), emo, hm));
+        hi = fmaf(cm, hi, fmaf(w * o1, emo, hp));
+        hj = fmaf(cm, hj, fmaf(-(w * o1), emo, hm));
+    }
+};
+
+template <class P, int FORCING>
+LBM_HD void collide_f_fast(float* h, const Macro& m, const Phys& ph)
+{
+    const FastF<P, FORCING> c(m, ph);
+    h[0] = c.rest(h[0]);
+    sfor<0, kPairs<typename P::LF>>([&](auto mc) {
+        constexpr int i = 2 * decltype(mc)::value + 1;
+        c.template pair<i>(h[i], h[i + 1]);
     });
 }
 
 template <class P>
+struct FastG {
+    using LG = typename P::LG;
+    static constexpr float c1 = LG::inv_cs2, c2 = LG::half_inv_cs4, c0 = LG::half_inv_cs2;
+    float om, cm;               // 1 / tau_g, 1 - 1 / tau_g
+    float ux, uy, uz, usq, rr, src, base, rho_p, obs, a2, a1;
+    LBM_HD FastG(const Macro& m, const Phys& ph)
+    {
+        om = 2.f - ph.delta_g;
+        cm = ph.delta_g - 1.f;
+        ux = m.ux; uy = m.uy; uz = m.uz;
+        usq = ux * ux + uy * uy + uz * uz;
+        rr = m.rho_p + ph.rho0;
+        src = ph.c_lbe * (-uz * ph.beta);                  // S_i / w_i (Eq. 12)
+        base = m.rho_p - c0 * rr * usq;
+        rho_p = m.rho_p;
+        obs = fmaf(om, base, src);
+        a2 = om * rr * c2;
+        a1 = om * rr * c1;
+    }
+    LBM_HD float rest(float k0) const
+    {
+        const float keq = LG::w(0) * base + LG::kMassCorr * rho_p + LG::kUsqCorr * rr * usq;
+        return fmaf(cm, k0, fmaf(om, keq, (LG::w(0) + LG::kMassCorr) * src));
+    }
+    template <int I>
+    LBM_HD void pair(float& ki, float& kj) const
+    {
+        constexpr float w = LG::w(I);
+        const float eu = e_dot<LG, I>(ux, uy, uz);
+        const float ks = fmaf((w * a2) * eu, eu, w * obs);
+        ki = fmaf(cm, ki, fmaf(w * a1, eu, ks));
+        kj = fmaf(cm, kj, fmaf(-(w * a1), eu, ks));
+    }
+};
+
+template <class P>
 LBM_HD void collide_g_fast(float* k, const Macro& m, const Phys& ph)
 {
-    using LG = typename P::LG;
-    constexpr float c1 = LG::inv_cs2, c2 = LG::half_inv_cs4, c0 = LG::half_inv_cs2;
-    const float om = 2.f - ph.delta_g;   // 1 / tau_g
-    const float cm = ph.delta_g - 1.f;   // 1 - 1 / tau_g
-    const float usq = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
-    const float rr = m.rho_p + ph.rho0;
-    const float src = ph.c_lbe * (-m.uz * ph.beta);                 // S_i / w_i (Eq. 12)
-    const float base = m.rho_p - c0 * rr * usq;
-    {
-        const float keq = LG::w(0) * base + LG::kMassCorr * m.rho_p + LG::kUsqCorr * rr * usq;
-        k[0] = fmaf(cm, k[0], fmaf(om, keq, (LG::w(0) + LG::kMassCorr) * src));
-    }
-    const float obs = fmaf(om, base, src);
-    const float a2 = om * rr * c2;
-    const float a1 = om * rr * c1;
-    sfor<0, kPairs<LG>>([&](auto mc) {
+    const FastG<P> c(m, ph);
+    k[0] = c.rest(k[0]);
+    sfor<0, kPairs<typename P::LG>>([&](auto mc) {
         constexpr int i = 2 * decltype(mc)::value + 1;
-        constexpr float w = LG::w(i);
-        const float eu = e_dot<LG, i>(m.ux, m.uy, m.uz);
-        const float ks = fmaf((w * a2) * eu, eu, w * obs);
-        k[i] = fmaf(cm, k[i], fmaf(w * a1, eu, ks));
-        k[i + 1] = fmaf(cm, k[i + 1], fmaf(-(w * a1), eu, ks));
+        c.template pair<i>(k[i], k[i + 1]);
     });
 }
 
