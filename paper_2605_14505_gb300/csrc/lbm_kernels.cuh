@@ -375,21 +375,12 @@ struct Seam {
 
 // Loads default-cached: the odd step writes each word back shortly after
 // reading it, and a word still in L2 takes the write without a miss.
-// A seam slot's word in a warp that holds a seam lane: its halves exchanged
-// on the seam lane (on), unchanged elsewhere. Two forms of the same result,
-// each the faster one for its storage type on the odd step at 256^3: a
-// byte permute with the lane's own selector (FP16: 0.4858 against
-// 0.4879 ms), a select between the word and its permutation (BF16: 0.4902
-// against 0.4984 ms).
-template <class T>
-__device__ __forceinline__ uint32_t seam_word(uint32_t w, bool on, uint32_t sel)
-{
-    if constexpr (std::is_same_v<T, __half>) {
-        return __byte_perm(w, 0u, sel);
-    } else {
-        return on ? __byte_perm(w, 0u, 0x1032u) : w;
-    }
-}
+// A seam slot's word in a warp that holds a seam lane: one byte permute with
+// the lane's own selector, which exchanges the halves on the seam lane and
+// keeps the word elsewhere (a select between the word and its permutation
+// gives the same words, measured slower: D3Q19xD3Q7 FP16 odd step 0.287
+// against 0.269 ms at 256^3).
+__device__ __forceinline__ uint32_t seam_word(uint32_t w, uint32_t sel) { return __byte_perm(w, 0u, sel); }
 
 __device__ __forceinline__ uint32_t ld_word(const unsigned short* p)
 {
@@ -400,7 +391,7 @@ __device__ __forceinline__ void st_word(unsigned short* p, uint32_t w)
     __stcs(reinterpret_cast<unsigned int*>(p), w);
 }
 
-template <class L, bool ODD, class T>
+template <class L, bool ODD>
 __device__ __forceinline__ void load_pair(const unsigned short* __restrict__ b16, uint32_t n3, const PairAddr& a,
                                           const Seam& sm, uint32_t* w)
 {
@@ -419,19 +410,19 @@ __device__ __forceinline__ void load_pair(const unsigned short* __restrict__ b16
         if (sm.warp_first) {
             sfor<0, L::kQ>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                if constexpr (L::ex(i) == 1) w[i] = seam_word<T>(w[i], sm.first, sm.sel_first);
+                if constexpr (L::ex(i) == 1) w[i] = seam_word(w[i], sm.sel_first);
             });
         }
         if (sm.warp_last) {
             sfor<0, L::kQ>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                if constexpr (L::ex(i) == -1) w[i] = seam_word<T>(w[i], sm.last, sm.sel_last);
+                if constexpr (L::ex(i) == -1) w[i] = seam_word(w[i], sm.sel_last);
             });
         }
     }
 }
 
-template <class L, bool ODD, class T>
+template <class L, bool ODD>
 __device__ __forceinline__ void store_pair(unsigned short* __restrict__ b16, uint32_t n3, const PairAddr& a,
                                            const Seam& sm, uint32_t* w)
 {
@@ -439,13 +430,13 @@ __device__ __forceinline__ void store_pair(unsigned short* __restrict__ b16, uin
         if (sm.warp_first) {
             sfor<0, L::kQ>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                if constexpr (L::ex(i) == -1) w[i] = seam_word<T>(w[i], sm.first, sm.sel_first);
+                if constexpr (L::ex(i) == -1) w[i] = seam_word(w[i], sm.sel_first);
             });
         }
         if (sm.warp_last) {
             sfor<0, L::kQ>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                if constexpr (L::ex(i) == 1) w[i] = seam_word<T>(w[i], sm.last, sm.sel_last);
+                if constexpr (L::ex(i) == 1) w[i] = seam_word(w[i], sm.sel_last);
             });
         }
     }
@@ -594,8 +585,8 @@ __device__ __forceinline__ void update_pair(const StepArgs& args, int x0, int y,
     const Seam sm(args.geo, x0);
     {
         const PairAddr a(args.geo, x0, y, z);
-        load_pair<typename P::LF, ODD, T>(fb, n3, a, sm, wf);
-        load_pair<typename P::LG, ODD, T>(gb, n3, a, sm, wg);
+        load_pair<typename P::LF, ODD>(fb, n3, a, sm, wf);
+        load_pair<typename P::LG, ODD>(gb, n3, a, sm, wg);
     }
     if constexpr (std::is_same_v<std::decay_t<Hook>, NoHook>) {
         collide_half_stream<P, FORCING, T, 0>(wf, wg, args.ph);
@@ -604,8 +595,8 @@ __device__ __forceinline__ void update_pair(const StepArgs& args, int x0, int y,
         collide_pair_words<P, FORCING, T>(wf, wg, args.ph, hook);
     }
     const PairAddr b(args.geo, (int)launder(x0), (int)launder(y), (int)launder(z));
-    store_pair<typename P::LF, ODD, T>(fb, n3, b, sm, wf);
-    store_pair<typename P::LG, ODD, T>(gb, n3, b, sm, wg);
+    store_pair<typename P::LF, ODD>(fb, n3, b, sm, wf);
+    store_pair<typename P::LG, ODD>(gb, n3, b, sm, wg);
 }
 
 // Three 256-thread blocks per SM (<= 85 registers) for D3Q27xD3Q19, whose

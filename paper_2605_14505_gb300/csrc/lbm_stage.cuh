@@ -169,7 +169,7 @@ __device__ __forceinline__ uint32_t lds_word(const uint16_t* p)
 // The pair's words of lattice L from its stage rows (rows = first row of L):
 // word p of the tile on the even step, word p - e_x on the odd step, with the
 // halves exchanged where the row wraps (as load_pair).
-template <class L, bool ODD, class T>
+template <class L, bool ODD>
 __device__ __forceinline__ void stage_load(const uint16_t* rows, int RS, int p, const Seam& sm, uint32_t* w)
 {
     sfor<0, L::kQ>([&](auto ic) {
@@ -181,13 +181,13 @@ __device__ __forceinline__ void stage_load(const uint16_t* rows, int RS, int p, 
         if (sm.warp_first) {
             sfor<0, L::kQ>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                if constexpr (L::ex(i) == 1) w[i] = seam_word<T>(w[i], sm.first, sm.sel_first);
+                if constexpr (L::ex(i) == 1) w[i] = seam_word(w[i], sm.sel_first);
             });
         }
         if (sm.warp_last) {
             sfor<0, L::kQ>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                if constexpr (L::ex(i) == -1) w[i] = seam_word<T>(w[i], sm.last, sm.sel_last);
+                if constexpr (L::ex(i) == -1) w[i] = seam_word(w[i], sm.sel_last);
             });
         }
     }
@@ -235,13 +235,13 @@ __global__ void __launch_bounds__(128, kStageMinBlocks<P>) k_step_staged(const _
             const int x0 = (int)(t - row * (uint32_t)A.ntx) * W + 2 * p;
             const Seam sm(A.geo, x0);
             uint32_t wf[P::QF], wg[P::QG];
-            stage_load<typename P::LF, ODD, T>(st, RS, p, sm, wf);
-            stage_load<typename P::LG, ODD, T>(st + (size_t)P::QF * RS, RS, p, sm, wg);
+            stage_load<typename P::LF, ODD>(st, RS, p, sm, wf);
+            stage_load<typename P::LG, ODD>(st + (size_t)P::QF * RS, RS, p, sm, wg);
             collide_pair_words<P, FORCING, T>(wf, wg, A.ph);
             const int y = (int)(row % (uint32_t)A.geo.ny), z = (int)(row / (uint32_t)A.geo.ny);
             const PairAddr b(A.geo, (int)launder(x0), (int)launder(y), (int)launder(z));
-            store_pair<typename P::LF, ODD, T>(fb, A.geo.n3, b, sm, wf);
-            store_pair<typename P::LG, ODD, T>(gb, A.geo.n3, b, sm, wg);
+            store_pair<typename P::LF, ODD>(fb, A.geo.n3, b, sm, wf);
+            store_pair<typename P::LG, ODD>(gb, A.geo.n3, b, sm, wg);
         }
         if (__syncthreads_or(!ok)) {
             // a wait ran out: report, let the copies in flight land, stop
