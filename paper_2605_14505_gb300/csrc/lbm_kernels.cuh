@@ -263,12 +263,16 @@ __device__ __forceinline__ void update_node(void* fv, void* gv, const Geometry& 
 // Three 256-thread blocks per SM (<= 85 registers): measured on the 256^3
 // D3Q27xD3Q19 lattice, 2% faster for FP32 Shan-Chen and 16% for FP16 with one
 // node per thread than the unconstrained allocation (up to 124 registers).
+// D3Q27xD3Q27, whose 54 values per node spill up to 180 bytes at that cap,
+// takes two (<= 128 registers).
 #ifndef LBM_STEP_MINBLOCKS
 #define LBM_STEP_MINBLOCKS 3
 #endif
+template <class P>
+constexpr int kStepMinBlocks = (P::QF + P::QG > 46) ? 2 : LBM_STEP_MINBLOCKS;
 // One AA step for every node of one lattice.
 template <class P, int FORCING, class T, bool ODD>
-__global__ void __launch_bounds__(256, LBM_STEP_MINBLOCKS) k_step(StepArgs args)
+__global__ void __launch_bounds__(256, kStepMinBlocks<P>) k_step(StepArgs args)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
