@@ -162,17 +162,20 @@ bool uses_pairs(const lbm_ctx* h, int odd)
 // candidate shapes at 256^3: the two-nodes-per-thread kernel runs best in
 // 128-thread blocks of 64 x 2, except on the odd steps of D3Q27xD3Q19, where
 // one row of 128 is faster (FP16 0.462 against 0.465 ms, BF16 0.462 against
-// 0.467 ms); the one-node kernels in blocks of one row of 256 threads for
-// D3Q27xD3Q19 and 128 for the smaller pairs, at either parity, and for
-// D3Q27xD3Q27 (two 128-register blocks per SM) one row of 64 on even steps
-// and 128 on odd steps (1.058 / 1.096 ms against 1.072 / 1.155 ms as 256).
+// 0.467 ms); the one-node kernels in one row of 256 threads on even steps
+// and on the odd steps of the pairs with 38 to 46 populations per node, one
+// row of 128 on the odd steps of the smaller pairs (D3Q19xD3Q7 0.515 / 0.528
+// ms, D3Q19xD3Q19 0.751 / 0.768 ms, against 0.520 / 0.528 and 0.758 / 0.776
+// as 128 on both), and for D3Q27xD3Q27 (two 128-register blocks per SM) one
+// row of 64 on even steps and 128 on odd steps (1.058 / 1.096 ms against
+// 1.072 / 1.155 ms as 256).
 void pick_block(const lbm_ctx* h, int odd, int& bx, int& by)
 {
     const bool pairs = uses_pairs(h, odd);
     const int xunits = pairs ? h->p.nx / 2 : h->p.nx;
-    const bool big = h->q.qf + h->q.qg >= 46;
-    const bool huge = h->q.qf + h->q.qg > 46;
-    const int threads = pairs ? 128 : huge ? (odd ? 128 : 64) : (big ? 256 : 128);
+    const int qsum = h->q.qf + h->q.qg;
+    const bool big = qsum >= 46;
+    const int threads = pairs ? 128 : qsum > 46 ? (odd ? 128 : 64) : (odd && qsum <= 34) ? 128 : 256;
     const int want = pairs ? ((odd && big) ? 128 : 64) : threads;
     bx = 32;
     while (bx * 2 <= want && bx * 2 <= xunits) bx *= 2;
