@@ -479,3 +479,44 @@ def test_energy_budget_laminar_tgv():
     rate = -(etot[2] - etot[0]) / (2 * dt)
     eps = e[1]["eps_k"] + e[1]["eps_p"]
     assert abs(rate / eps - 1) < 0.03, (rate, eps)
+
+
+@pytest.mark.parametrize("tau_f", [1.0, 0.8])
+@pytest.mark.parametrize("forcing", ["guo", "sc", "edm", "hcz"])
+@pytest.mark.parametrize("pair", [(27, 19), (19, 7)])
+def test_uniform_acceleration_has_no_strain(pair, forcing, tau_f):
+    """Strain-rate estimator of eps_k (Eq. 25 read through the non-equilibrium
+    second moment, forcing of Eq. 18). A uniform state on a periodic lattice
+    stays uniform, so its velocity field has no gradient and the exact
+    dissipation is zero. The force still leaves a non-equilibrium stress
+    behind: after the BGK memory (1 - 1/tau_f)^t has died out, Pi_neq equals
+    -(u F + F u)/2 (exactly for Guo, up to O(F^2) for the shift schemes and
+    HCZ), which the estimator's forcing correction must cancel. With beta = 0
+    the scalar source vanishes, rho' and F = (0, 0, -G rho') stay constant and
+    the momentum grows by F per step. The estimator must give zero to a tiny
+    fraction of what the correction term alone contributes; dropping that term
+    gives the full contribution and flipping its sign four times it."""
+    qf, qg = pair
+    n, G, rho_val, rp_val = 4, 1e-3, 1.01, 0.1
+    u0 = np.array([0.05, -0.03, 0.0])
+    p = O.lattice_params(n, n, n, qf, qg, forcing, tau_f, 0.7, G, 0.0)
+    s = O.OracleSim(p)
+    n3 = n ** 3
+    s.init_fields(np.full(n3, rho_val), np.repeat(u0[:, None], n3, axis=1), np.full(n3, rp_val))
+    steps = 3 if tau_f == 1.0 else 40
+    s.step(steps)
+    d = s.diagnostics()
+    # closed forms: rho conserved, j = rho u0 + t F (the equilibrium start holds
+    # momentum rho u0), physical u = (j + F/2) / rho (Eq. 7)
+    cs2 = 1.0 / 3.0
+    F = np.array([0.0, 0.0, -G * rp_val])
+    u = (rho_val * u0 + steps * F + 0.5 * F) / rho_val
+    nu = cs2 * (tau_f - 0.5)
+    corr = 0.5 * (np.outer(u, F) + np.outer(F, u)) / (2.0 * rho_val * cs2 * tau_f)
+    eps_corr = 2.0 * nu * float((corr * corr).sum())
+    assert eps_corr > 1e-13
+    assert 0.0 <= d["eps_k"] < 1e-4 * eps_corr, (d["eps_k"], eps_corr)
+    # the state is uniform and the velocity is the closed form
+    _, uf, rpf = s.fields()
+    assert np.allclose(uf, u[:, None], rtol=0, atol=1e-15)
+    assert np.allclose(rpf, rp_val, rtol=0, atol=1e-14)
