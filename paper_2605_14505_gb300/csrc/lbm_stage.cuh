@@ -18,8 +18,13 @@
 // tiles b, b + grid, ...
 //
 // Every mbarrier wait is bounded (spin_limit polls). A wait that runs out
-// raises *err; the block then waits, again bounded, for its copies still in
-// flight and returns, so a barrier that cannot complete ends the kernel.
+// raises *err; the block then drains: it waits for the barriers of the copies
+// it has issued, with its own fixed limit (kStageDrainPolls, independent of
+// spin_limit), and returns, so a barrier that cannot complete ends the kernel
+// and no bulk copy is still writing shared memory when the block exits. The
+// test hook's phantom bytes are counted on a barrier of their own that no
+// copy signals, so the real copies' barriers always complete and the drain
+// observes every copy landing.
 #pragma once
 
 #include "lbm_kernels.cuh"
@@ -36,16 +41,20 @@ struct StageArgs {
     uint32_t ntiles;        // ntx * ny * nz
     int* err;               // set to 1 when a wait gives up
     uint32_t spin_limit;    // polls per wait
-    uint32_t extra_tx;      // test hook: bytes expected beyond the copies (0 in use)
+    uint32_t extra_tx;      // test hook: bytes a separate barrier expects and no copy delivers (0 in use)
 };
+
+// Polls of the drain after a wait ran out: long enough for any copy in
+// flight to land (~0.3-1 s), and bounded so that the block always returns.
+constexpr uint32_t kStageDrainPolls = 1u << 22;
 
 constexpr int kStagePad = 8;   // staged row element j holds row element xs - 8 + j
 
 // Shared-memory bytes of one block: two stages of Q rows of W + 16 elements,
-// two mbarriers, Q row codes.
+// three mbarriers (one per stage, one for the test hook), Q row codes.
 __host__ __device__ constexpr size_t stage_smem_bytes(int q, int W)
 {
-    return (size_t)2 * q * (W + 2 * kStagePad) * 2 + 16 + (size_t)q * 4;
+    return (size_t)2 * q * (W + 2 * kStagePad) * 2 + 24 + (size_t)q * 4;
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
@@ -136,7 +145,7 @@ __device__ __forceinline__ void stage_issue(const StageArgs& A, uint16_t* st, ui
     const int y = (int)(row % (uint32_t)ny), z = (int)(row / (uint32_t)ny);
     const int xs = (int)xt * W;
     const uint32_t row_bytes = (uint32_t)(ODD ? W + 2 * kStagePad : W) * 2u;
-    if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)Q * row_bytes + A.extra_tx);
+    if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)Q * row_bytes);
     __syncwarp();
     const uint16_t* base = static_cast<const uint16_t*>(A.f);
     for (int r = lane; r < Q; r += 32) {
@@ -204,11 +213,14 @@ __global__ void __launch_bounds__(128, kStageMinBlocks<P>) k_step_staged(const _
     const int W = A.W, RS = W + 2 * kStagePad;
     uint16_t* stages = reinterpret_cast<uint16_t*>(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)2 * Q * RS * 2);
-    uint32_t* code = reinterpret_cast<uint32_t*>(bar + 2);
+    uint32_t* code = reinterpret_cast<uint32_t*>(bar + 3);
     for (int r = (int)threadIdx.x; r < Q; r += (int)blockDim.x) code[r] = stage_row_code<P, ODD>(r);
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
+        mbar_init(&bar[2], 1);
+        // test hook: phase 0 of bar[2] expects bytes that no copy delivers
+        if (A.extra_tx) mbar_arrive_expect_tx(&bar[2], A.extra_tx);
         fence_mbarrier_init();
     }
     __syncthreads();
@@ -228,7 +240,8 @@ __global__ void __launch_bounds__(128, kStageMinBlocks<P>) k_step_staged(const _
             fence_proxy_async_smem();
             stage_issue<P, ODD>(A, stages + (size_t)(s ^ 1u) * Q * RS, &bar[s ^ 1u], code, tn);
         }
-        const bool ok = mbar_wait(&bar[s], (k >> 1) & 1u, A.spin_limit);
+        bool ok = mbar_wait(&bar[s], (k >> 1) & 1u, A.spin_limit);
+        if (A.extra_tx && ok) ok = mbar_wait(&bar[2], 0u, A.spin_limit);
         if (ok) {
             const uint16_t* st = stages + (size_t)s * Q * RS;
             const uint32_t row = t / (uint32_t)A.ntx;
@@ -244,10 +257,11 @@ __global__ void __launch_bounds__(128, kStageMinBlocks<P>) k_step_staged(const _
             store_pair<typename P::LG, ODD>(gb, A.geo.n3, b, sm, wg);
         }
         if (__syncthreads_or(!ok)) {
-            // a wait ran out: report, let the copies in flight land, stop
+            // a wait ran out: report, wait for this block's copies in flight
+            // (the two stage barriers; the hook's barrier has none), stop
             if (threadIdx.x == 0) atomicExch(A.err, 1);
-            mbar_wait(&bar[s], (k >> 1) & 1u, A.spin_limit);
-            if (tn < A.ntiles) mbar_wait(&bar[s ^ 1u], ((k + 1) >> 1) & 1u, A.spin_limit);
+            mbar_wait(&bar[s], (k >> 1) & 1u, kStageDrainPolls);
+            if (tn < A.ntiles) mbar_wait(&bar[s ^ 1u], ((k + 1) >> 1) & 1u, kStageDrainPolls);
             return;
         }
     }

@@ -140,12 +140,19 @@ def test_staged_wait_timeout_returns_an_error_and_the_context_survives():
     lbm.lbm_set_tile_staging(s.h, True)
     s.init_tgv(seed=1, noise_amp=1e-3)
     assert lbm.lbm_uses_tile_staging(s.h) == 64
-    # every tile expects 16 bytes that no copy delivers; each wait gives up after 20000 polls
-    lbm.lbm_set_stage_test(s.h, 16, 20000)
-    s.step(2)
+    # each block also waits on a barrier that expects 16 bytes no copy
+    # delivers; with 64 polls per wait even the waits on the real copies
+    # usually run out first. Either way the block drains its own copies (a
+    # fixed limit of its own) before it returns.
+    for spin in (64, 20000):
+        lbm.lbm_set_stage_test(s.h, 16, spin)
+        s.step(2)
+        with pytest.raises(lbm.LbmError) as ei:
+            s.synchronize()
+        assert ei.value.code == -4  # LBM_ETIMEOUT
     with pytest.raises(lbm.LbmError) as ei:
-        s.synchronize()
-    assert ei.value.code == -4  # LBM_ETIMEOUT
+        lbm.lbm_set_stage_test(s.h, 1 << 20, 64)
+    assert ei.value.code == -1
     lbm.lbm_set_stage_test(s.h, 0, 1 << 22)
     s.init_tgv(seed=1, noise_amp=1e-3)
     s.step(4)
