@@ -95,8 +95,13 @@ typedef struct lbm_params {
     double L;                /* reference length L = 1 in lattice spacings (reporting only) */
 } lbm_params;
 
-/* Diagnostics of the current state (post-stream, pre-collision), lattice
- * units, averages over all nodes (Eqs. 22-26). */
+/* Diagnostics of the current state (post-stream, pre-collision), averages
+ * over all nodes (Eqs. 22-26). The first block is in lattice units. The
+ * second gives the same quantities in the paper's units (Section 2.4: the
+ * reference velocity and length are 1, so the convective time is L / U0 time
+ * steps), from the handle's U0 and L (lattice units): t = step U0 / L,
+ * energies / U0^2, dissipation rates * L / U0^3. Those are NaN when U0 or L
+ * is not positive (lattice parameters made without them). */
 typedef struct lbm_diag {
     double Ek;          /* <|u|^2 / 2>, u of Eq. 7 (Eq. 22) */
     double Ep;          /* <(G/N)^2 (rho'/rho0)^2 / 2> (Eq. 23) */
@@ -108,6 +113,13 @@ typedef struct lbm_diag {
     double mom[3];      /* sum over nodes and slots of e_i f_i */
     double umax;        /* max |u| */
     int64_t step;       /* time steps taken since initialisation */
+    /* paper units */
+    double t;           /* step * U0 / L (convective times) */
+    double Ek_phys;     /* Ek / U0^2 */
+    double Ep_phys;     /* Ep / U0^2 */
+    double eps_k_phys;  /* eps_k * L / U0^3 */
+    double eps_p_phys;  /* eps_p * L / U0^3 */
+    double eps_k_curl_phys;  /* eps_k_curl * L / U0^3 */
 } lbm_diag;
 
 typedef struct lbm_ctx* lbm_handle;
@@ -266,8 +278,12 @@ int lbm_step_count(lbm_handle h, int64_t* step);
  * Scratch: one file-scope device array of 4096 x 11 doubles (~360 KB) that
  * every GPU loading this library holds until the process exits. It limits the
  * lattice to 4096 * 32768 = 134,217,728 nodes (512^3); larger lattices give
- * LBM_EINVAL. The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * LBM_EINVAL. The array's device address is looked up (cudaGetSymbolAddress)
+ * when a handle is created and, if that lookup failed, on the first call on
+ * the device, so make that first call before any stream capture. A device
+ * reset destroys every handle; handles created after it look the address up
+ * again. The moment pass runs on at least 4 blocks per SM (as
+ * lbm_diagnostics), at most one block per 256 nodes.
  * All calls share the array, which keeps the last call's contents: calls that
  * overlap on the GPU (several handles or threads, different streams) race and
  * must be serialised by the caller. Waits for the handle's stream. */
@@ -319,10 +335,15 @@ int lbm_set_tile_staging(lbm_handle h, int enable);
  * staging disabled, or no store yet). */
 int lbm_uses_tile_staging(lbm_handle h, int* width);
 
-/* Test hook for the bounded waits of tile staging: every tile expects
- * extra_tx_bytes more than its copies deliver (so with extra_tx_bytes > 0 no
- * wait can complete) and each wait polls at most spin_limit times. (0, 1 << 22)
- * restores normal operation. Error: LBM_EINVAL for spin_limit = 0. */
+/* Test hook for the bounded waits of tile staging: with extra_tx_bytes > 0
+ * each block also waits, after its copies of a tile have landed, on a barrier
+ * of its own that expects extra_tx_bytes which no copy delivers, so that wait
+ * runs out; every wait polls at most spin_limit times. A block whose wait ran
+ * out raises the error flag and then waits for its own bulk copies still in
+ * flight with a fixed limit of its own (about 0.3-1 s, independent of
+ * spin_limit) before it exits, so no copy writes shared memory after the
+ * block has ended. (0, 1 << 22) restores normal operation. Errors:
+ * LBM_EINVAL for spin_limit = 0 or extra_tx_bytes >= 2^20. */
 int lbm_set_stage_test(lbm_handle h, unsigned extra_tx_bytes, unsigned spin_limit);
 
 /* Enable (1, default) or disable (0) CUDA-graph replay in lbm_step. */

@@ -64,6 +64,10 @@ size_t elem_size(int storage) { return storage == LBM_FP32 ? 4 : 2; }
 
 constexpr int kGraphSteps = 64;   // even number: the graph starts and ends in natural layout
 
+// Looks up (again) the device address of the allocation-free diagnostics
+// scratch on `device`, which must be current; defined with the array below.
+void static_scratch_refresh(int device);
+
 }  // namespace
 
 struct lbm_ctx {
@@ -89,7 +93,7 @@ struct lbm_ctx {
     int stage_grid = 0;               // persistent grid of the staged kernel (0: not derived yet)
     int* d_err = nullptr;             // device flag raised by a bounded wait that ran out
     uint32_t stage_spin = 1u << 22;   // mbarrier polls per wait
-    uint32_t stage_extra_tx = 0;      // test hook: bytes expected beyond the copies
+    uint32_t stage_extra_tx = 0;      // test hook: bytes a barrier of their own expects and no copy delivers
     // diagnostics scratch
     float* diag_fields = nullptr;
     double* diag_partials = nullptr;
@@ -298,6 +302,23 @@ DiagArgs diag_args(lbm_ctx* h)
     return a;
 }
 
+// The paper-unit block of a record (Section 2.4: U = L = 1, so one
+// convective time is L / U0 steps): t = step U0 / L, energies / U0^2,
+// dissipation rates * L / U0^3; NaN without a positive U0 and L.
+void fill_phys(const lbm_params& p, lbm_diag* out)
+{
+    const bool ok = p.U0 > 0.0 && p.L > 0.0 && std::isfinite(p.U0) && std::isfinite(p.L);
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    const double e = ok ? 1.0 / (p.U0 * p.U0) : nan;
+    const double r = ok ? p.L / (p.U0 * p.U0 * p.U0) : nan;
+    out->t = ok ? (double)out->step * p.U0 / p.L : nan;
+    out->Ek_phys = out->Ek * e;
+    out->Ep_phys = out->Ep * e;
+    out->eps_k_phys = out->eps_k * r;
+    out->eps_p_phys = out->eps_p * r;
+    out->eps_k_curl_phys = out->eps_k_curl * r;
+}
+
 // Totals (diag_host) -> lbm_diag of the state at `step`.
 int fill_diag(const lbm_ctx* h, int64_t step, lbm_diag* out)
 {
@@ -315,6 +336,7 @@ int fill_diag(const lbm_ctx* h, int64_t step, lbm_diag* out)
     out->mom[2] = s[kDJz];
     out->umax = s[kDUmax];
     out->step = step;
+    fill_phys(h->p, out);
     for (int q = 0; q < kDNumSlots; ++q)
         if (!std::isfinite(s[q])) return fail(LBM_ENONFINITE, "non-finite diagnostics at step %lld", (long long)step);
     return LBM_OK;
@@ -501,6 +523,9 @@ int lbm_create_params(lbm_handle* out, const lbm_params* p)
     h->ks = ks;
     h->device = dev;
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    // a device reset ends every handle, so looking the scratch address up
+    // again here keeps the cached one valid for every handle in use
+    static_scratch_refresh(dev);
     derive_phys(h);
     default_block(h);
     e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
@@ -1110,6 +1135,7 @@ int lbm_set_stage_test(lbm_handle h, unsigned extra_tx_bytes, unsigned spin_limi
 {
     if (!h) return fail(LBM_EINVAL, "null handle");
     if (spin_limit == 0) return fail(LBM_EINVAL, "spin_limit must be positive");
+    if (extra_tx_bytes >= (1u << 20)) return fail(LBM_EINVAL, "extra_tx_bytes must be below 2^20 (mbarrier tx count)");
     h->stage_extra_tx = extra_tx_bytes;
     h->stage_spin = spin_limit;
     drop_graph(h);
@@ -1130,7 +1156,10 @@ int lbm_set_graphs(lbm_handle h, int enable)
 // Allocation-free diagnostics: the block partials of the moment pass and the
 // final sums live in this file-scope device array instead of cudaMalloc'ed
 // scratch. Host code cannot use the array's name as a device address, so the
-// address is looked up once per device and cached.
+// address is looked up with the device current and cached per device: when a
+// handle is created (lbm_create_params) and, if still missing, on the first
+// allocation-free call. A device reset destroys every handle, and the handles
+// made after it look the address up again when they are created.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int kStaticMaxBlocks = 4096;
@@ -1144,6 +1173,16 @@ double* g_static_addr[kStaticMaxDevices] = {};
 static __device__ __align__(256) double g_static_scratch[kStaticOutOffset + 16];
 
 namespace {
+void static_scratch_refresh(int device)
+{
+    if (device < 0 || device >= kStaticMaxDevices) return;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) cudaGetLastError();
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    g_static_addr[device] = (e == cudaSuccess) ? static_cast<double*>(p) : nullptr;
+}
+
 int static_scratch_address(int device, double** out)
 {
     if (device < 0 || device >= kStaticMaxDevices) return fail(LBM_EUNSUPPORTED, "device %d out of range", device);
@@ -1167,8 +1206,8 @@ int lbm_diagnostics_noalloc(lbm_handle h, lbm_diag* out)
     if (rc) return rc;
     if (!out) return fail(LBM_EINVAL, "null output");
     const uint32_t n3 = h->geo.n3;
-    const uint32_t blocks = (n3 + kStaticNodesPerBlock - 1) / kStaticNodesPerBlock;
-    if (blocks > (uint32_t)kStaticMaxBlocks)
+    const uint32_t min_blocks = (n3 + kStaticNodesPerBlock - 1) / kStaticNodesPerBlock;
+    if (min_blocks > (uint32_t)kStaticMaxBlocks)
         return fail(LBM_EINVAL,
                     "lattice of %u nodes exceeds the static diagnostics scratch (at most %u nodes); "
                     "use lbm_diagnostics",
@@ -1176,6 +1215,12 @@ int lbm_diagnostics_noalloc(lbm_handle h, lbm_diag* out)
     if (!h->initialized) return fail(LBM_ESTATE, "diagnostics before initialisation");
     double* scratch = nullptr;
     if ((rc = static_scratch_address(h->device, &scratch))) return rc;
+    // the moment pass strides over the lattice, so the grid fills the GPU
+    // (4 blocks per SM, as lbm_diagnostics) whatever the node count, within
+    // the array's rows and without blocks that get no node
+    const uint32_t sms = (uint32_t)(h->num_sms > 0 ? h->num_sms : 132);
+    const uint32_t busy = std::min(4 * sms, (n3 + kDiagBlock - 1) / (uint32_t)kDiagBlock);
+    const uint32_t blocks = std::min((uint32_t)kStaticMaxBlocks, std::max(min_blocks, busy));
     const lbm_params& p = h->p;
     const double cs2f = cs2_of(h->q.qf);
     const double gn2 = (p.beta != 0.0) ? (-p.G * p.rho0 / p.beta) : 1.0;
@@ -1220,6 +1265,7 @@ int lbm_diagnostics_noalloc(lbm_handle h, lbm_diag* out)
     out->mom[2] = s[kDJz];
     out->umax = s[kDUmax];
     out->step = h->step;
+    fill_phys(p, out);
     for (int q = 0; q < kDiagPass1; ++q)
         if (!std::isfinite(s[q])) return fail(LBM_ENONFINITE, "non-finite diagnostics at step %lld", (long long)h->step);
     return LBM_OK;

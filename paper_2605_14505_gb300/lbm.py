@@ -58,6 +58,9 @@ class lbm_diag(ctypes.Structure):
         ("eps_p", ctypes.c_double), ("eps_k_curl", ctypes.c_double),
         ("mass_f", ctypes.c_double), ("mass_g", ctypes.c_double),
         ("mom", ctypes.c_double * 3), ("umax", ctypes.c_double), ("step", ctypes.c_int64),
+        ("t", ctypes.c_double), ("Ek_phys", ctypes.c_double), ("Ep_phys", ctypes.c_double),
+        ("eps_k_phys", ctypes.c_double), ("eps_p_phys", ctypes.c_double),
+        ("eps_k_curl_phys", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -66,6 +69,9 @@ class lbm_diag(ctypes.Structure):
             "eps_k_curl": self.eps_k_curl, "mass_f": self.mass_f, "mass_g": self.mass_g,
             "mom_x": self.mom[0], "mom_y": self.mom[1], "mom_z": self.mom[2],
             "umax": self.umax, "step": int(self.step),
+            "t": self.t, "Ek_phys": self.Ek_phys, "Ep_phys": self.Ep_phys,
+            "eps_k_phys": self.eps_k_phys, "eps_p_phys": self.eps_p_phys,
+            "eps_k_curl_phys": self.eps_k_curl_phys,
         }
 
 

@@ -1,9 +1,9 @@
 """Post-processing of the diagnostics time series (paper Sections 3.3-3.5).
 
 These are host-side reductions of a few numbers per sample, not part of the
-GPU update. Lattice-unit diagnostics (lbm_diag) are converted to the paper's
-units with U = L = 1: time t = step * U0 / L_LB, energies / U0^2,
-dissipation rates * L_LB / U0^3, where L_LB = n / (2 pi).
+GPU update. The paper's units have U = L = 1: time t = step * U0 / L_LB,
+energies / U0^2, dissipation rates * L_LB / U0^3, where L_LB = n / (2 pi);
+the library's diagnostics records already carry those values.
 """
 from __future__ import annotations
 
@@ -12,14 +12,30 @@ import numpy as np
 _trapezoid = getattr(np, "trapezoid", None) or np.trapz
 
 
-def to_physical(series, U0: float, L: float) -> dict:
-    """Convert a list of lbm_diag dicts to arrays in the paper's units."""
-    step = np.array([d["step"] for d in series], dtype=np.float64)
-    out = {"t": step * U0 / L}
-    for key in ("Ek", "Ep"):
-        out[key] = np.array([d[key] for d in series]) / U0 ** 2
-    for key in ("eps_k", "eps_p", "eps_k_curl"):
-        out[key] = np.array([d[key] for d in series]) * L / U0 ** 3
+def to_physical(series, U0: float | None = None, L: float | None = None) -> dict:
+    """Arrays of a diagnostics time series in the paper's units.
+
+    Records from the library carry the paper-unit values themselves (lbm_diag:
+    t, Ek_phys, ..., computed in the C library from the handle's U0 and L);
+    those are used as they are. Records without them (or with NaN there, for
+    lattice parameters made without U0 and L) are converted from the lattice
+    values with the given U0 and L."""
+    def have(d):
+        return "t" in d and np.isfinite(d["t"])
+
+    if all(have(d) for d in series):
+        out = {"t": np.array([d["t"] for d in series], dtype=np.float64)}
+        for key in ("Ek", "Ep", "eps_k", "eps_p", "eps_k_curl"):
+            out[key] = np.array([d[key + "_phys"] for d in series], dtype=np.float64)
+    else:
+        if U0 is None or L is None:
+            raise ValueError("records without paper-unit values need U0 and L")
+        step = np.array([d["step"] for d in series], dtype=np.float64)
+        out = {"t": step * U0 / L}
+        for key in ("Ek", "Ep"):
+            out[key] = np.array([d[key] for d in series]) / U0 ** 2
+        for key in ("eps_k", "eps_p", "eps_k_curl"):
+            out[key] = np.array([d[key] for d in series]) * L / U0 ** 3
     out["Etot"] = out["Ek"] + out["Ep"]          # Eq. 24
     return out
 

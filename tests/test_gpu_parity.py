@@ -172,6 +172,13 @@ def test_c0_diagnostics_series():
         # ~2e-9 per node per step over 32^3 nodes and 200 steps is ~6e-6
         for key in ("mom_x", "mom_y", "mom_z"):
             assert abs(dg[key] - do[key]) < 5e-5
+        # the paper-unit block (Section 2.4: U = L = 1) from the handle's U0, L
+        U0, L = p.U0, p.L
+        assert abs(dg["t"] - do["step"] * U0 / L) < 1e-15 * (1 + dg["t"])
+        for key in ("Ek", "Ep"):
+            assert dg[key + "_phys"] == pytest.approx(dg[key] / U0 ** 2, rel=1e-15)
+        for key in ("eps_k", "eps_p", "eps_k_curl"):
+            assert dg[key + "_phys"] == pytest.approx(dg[key] * L / U0 ** 3, rel=1e-15)
 
 
 @pytest.mark.parametrize("storage,tol", [("fp16", 0.01), ("bf16", 0.05)])

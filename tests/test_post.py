@@ -15,6 +15,12 @@ def test_unit_conversion_and_total_energy():
     assert np.allclose(d["Ek"], 2e-4 / U0 ** 2)
     assert np.allclose(d["eps_k"], 1e-8 * L / U0 ** 3)
     assert np.allclose(d["Etot"], d["Ek"] + d["Ep"])
+    # records that carry their own paper-unit values are taken as they are
+    phys = [dict(r, t=r["step"] * 1e-3, Ek_phys=1.0, Ep_phys=2.0, eps_k_phys=3.0, eps_p_phys=4.0,
+                 eps_k_curl_phys=5.0) for r in series]
+    d2 = post.to_physical(phys)
+    assert np.allclose(d2["t"], [0.0, 0.1, 0.2]) and np.allclose(d2["Etot"], 3.0)
+    assert np.allclose(d2["eps_p"], 4.0)
 
 
 def test_central_difference_is_exact_on_quadratics():

@@ -29,10 +29,15 @@ def _close(a, b, rel=1e-10, abs_=1e-12):
     return abs(a - b) <= rel * max(abs(a), abs(b)) + abs_
 
 
-def test_noalloc_diagnostics_match_two_calls_in_a_row():
+@pytest.mark.parametrize("pair", ["27x19", "19x7"])
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_noalloc_diagnostics_match_two_calls_in_a_row(storage, pair):
+    """FP32 and FP16 stores (the latter in the half-row order, read through the
+    same node addressing), the D3Q27xD3Q19 pair and the D3Q19xD3Q7 pair (whose
+    D3Q7 scalar set takes the diagnostics' explicit-equilibrium branch)."""
     n = 48
-    p = lbm.lbm_params_from_physics(n, n, n, "27x19", "sc", 200.0, 0.2, 1.0, 0.04)
-    sim = lbm.Simulation(p)
+    p = lbm.lbm_params_from_physics(n, n, n, pair, "sc", 200.0, 0.2, 1.0, 0.04)
+    sim = lbm.Simulation(p, storage=storage)
     sim.init_tgv(seed=11, noise_amp=0.01)
     for steps in (37, 13):  # odd layout first, then the natural layout
         sim.step(steps)
@@ -44,6 +49,22 @@ def test_noalloc_diagnostics_match_two_calls_in_a_row():
         for key in ("mom_x", "mom_y", "mom_z"):
             assert _close(got[key], ref[key], abs_=1e-6), (key, got[key], ref[key])
         assert math.isnan(got["eps_p"]) and math.isnan(got["eps_k_curl"])
+        assert got["t"] == ref["t"] and got["Ek_phys"] == pytest.approx(ref["Ek_phys"], rel=1e-10)
+    sim.close()
+
+
+def test_noalloc_diagnostics_small_lattice():
+    """A lattice smaller than one block of nodes per SM: fewer blocks than the
+    4-per-SM grid, none of them without nodes."""
+    n = 8
+    p = lbm.lbm_params_from_physics(n, n, n, "27x19", "guo", 100.0, 0.5, 1.0, 0.04)
+    sim = lbm.Simulation(p)
+    sim.init_tgv(seed=3, noise_amp=0.01)
+    sim.step(5)
+    ref = sim.diagnostics()
+    got = lbm.lbm_diagnostics_noalloc(sim.h)
+    for key in KEYS:
+        assert _close(got[key], ref[key]), (key, got[key], ref[key])
     sim.close()
 
 
