@@ -289,6 +289,36 @@ int lbm_step_count(lbm_handle h, int64_t* step);
  * must be serialised by the caller. Waits for the handle's stream. */
 int lbm_diagnostics_noalloc(lbm_handle h, lbm_diag* out);
 
+/* The 16-bit storage rule. FP16 or BF16 deviation storage (FP32 arithmetic)
+ * serves a workload only while its energy and dissipation series (Eqs. 22-26:
+ * E_k, E_p, eps_k, eps_p) stay within tol (0.01 in the precision target) of a
+ * reference series of the same workload: the FP64 oracle where one can be
+ * computed, else the FP32-storage run on the same GPU; otherwise FP32 storage
+ * is the fallback. The comparison:
+ *  - per quantity, max over samples |cand - ref| / max over samples |ref|
+ *    (the series maximum as scale, since E_p and eps_p start at zero);
+ *  - the total dissipation eps_k + eps_p at the two highest interior local
+ *    maxima of the reference series (the double peak of Section 3.3), each
+ *    relative to its own height (skipped where the reference has fewer
+ *    peaks).
+ * ref[count] and cand[count] are records of the same steps (LBM_EINVAL if a
+ * step differs or a reference value is not finite); a non-finite candidate
+ * value fails the rule. candidate_storage is an enum lbm_storage. Returns the
+ * storage to use (candidate_storage if every deviation is <= tol, else
+ * LBM_FP32), or a negative LBM_E* code; report (may be NULL) receives the
+ * deviations. Host-only: no device work. */
+typedef struct lbm_storage_report {
+    double dev_Ek, dev_Ep, dev_eps_k, dev_eps_p;   /* max |cand - ref| / max |ref| */
+    double dev_peak1, dev_peak2;   /* |cand - ref| / ref of eps_k + eps_p at the highest and the
+                                      second-highest reference peak (NaN: no such peak) */
+    int64_t step_peak1, step_peak2;   /* their steps (-1: no such peak) */
+    int32_t selected;                 /* enum lbm_storage */
+    int32_t pass;                     /* 1 if every deviation is <= tol */
+} lbm_storage_report;
+
+int lbm_storage_rule(const lbm_diag* ref, const lbm_diag* cand, int64_t count, int candidate_storage,
+                     double tol, lbm_storage_report* report);
+
 /* Launch shape of the step kernel (threads along x and y; bx * by <= 256,
  * bx a multiple of 32). With two nodes per thread (lbm_set_pairing) a
  * thread along x covers two nodes. Each AA parity has its own shape:

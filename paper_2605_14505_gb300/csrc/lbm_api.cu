@@ -1883,3 +1883,83 @@ int lbm_batch_destroy(lbm_batch b)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// The 16-bit storage rule (host logic on a few numbers per sample).
+// ---------------------------------------------------------------------------
+namespace {
+
+// max_s |c_s - r_s| / max_s |r_s| of one diagnostics quantity; +inf when the
+// candidate is not finite, 0 for an all-zero reference matched exactly.
+template <class Get>
+double series_dev(const lbm_diag* ref, const lbm_diag* cand, int64_t count, Get get)
+{
+    double scale = 0.0, worst = 0.0;
+    for (int64_t s = 0; s < count; ++s) {
+        const double r = get(ref[s]), c = get(cand[s]);
+        if (!std::isfinite(c)) return std::numeric_limits<double>::infinity();
+        scale = std::max(scale, std::fabs(r));
+        worst = std::max(worst, std::fabs(c - r));
+    }
+    if (scale > 0.0) return worst / scale;
+    return worst > 0.0 ? std::numeric_limits<double>::infinity() : 0.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_storage_rule(const lbm_diag* ref, const lbm_diag* cand, int64_t count, int candidate_storage, double tol,
+                     lbm_storage_report* report)
+{
+    if (!ref || !cand || count < 1) return fail(LBM_EINVAL, "lbm_storage_rule needs two series of >= 1 samples");
+    if (candidate_storage < LBM_FP32 || candidate_storage > LBM_BF16_DEV)
+        return fail(LBM_EINVAL, "unknown storage %d", candidate_storage);
+    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(LBM_EINVAL, "tol must be finite and > 0");
+    for (int64_t s = 0; s < count; ++s) {
+        if (ref[s].step != cand[s].step)
+            return fail(LBM_EINVAL, "sample %lld: reference step %lld, candidate step %lld", (long long)s,
+                        (long long)ref[s].step, (long long)cand[s].step);
+        if (!std::isfinite(ref[s].Ek) || !std::isfinite(ref[s].Ep) || !std::isfinite(ref[s].eps_k) ||
+            !std::isfinite(ref[s].eps_p))
+            return fail(LBM_EINVAL, "reference sample %lld is not finite", (long long)s);
+    }
+    lbm_storage_report r{};
+    r.dev_Ek = series_dev(ref, cand, count, [](const lbm_diag& d) { return d.Ek; });
+    r.dev_Ep = series_dev(ref, cand, count, [](const lbm_diag& d) { return d.Ep; });
+    r.dev_eps_k = series_dev(ref, cand, count, [](const lbm_diag& d) { return d.eps_k; });
+    r.dev_eps_p = series_dev(ref, cand, count, [](const lbm_diag& d) { return d.eps_p; });
+    // the two highest interior local maxima of the reference eps_k + eps_p
+    auto eps = [](const lbm_diag& d) { return d.eps_k + d.eps_p; };
+    int64_t p1 = -1, p2 = -1;
+    for (int64_t s = 1; s + 1 < count; ++s) {
+        const double e = eps(ref[s]);
+        if (!(e > eps(ref[s - 1]) && e >= eps(ref[s + 1]))) continue;
+        if (p1 < 0 || e > eps(ref[p1])) {
+            p2 = p1;
+            p1 = s;
+        } else if (p2 < 0 || e > eps(ref[p2])) {
+            p2 = s;
+        }
+    }
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    auto peak_dev = [&](int64_t s) {
+        if (s < 0) return nan;
+        const double c = eps(cand[s]);
+        if (!std::isfinite(c)) return std::numeric_limits<double>::infinity();
+        return std::fabs(c - eps(ref[s])) / std::fabs(eps(ref[s]));
+    };
+    r.dev_peak1 = peak_dev(p1);
+    r.dev_peak2 = peak_dev(p2);
+    r.step_peak1 = p1 < 0 ? -1 : ref[p1].step;
+    r.step_peak2 = p2 < 0 ? -1 : ref[p2].step;
+    bool pass = r.dev_Ek <= tol && r.dev_Ep <= tol && r.dev_eps_k <= tol && r.dev_eps_p <= tol;
+    if (p1 >= 0) pass = pass && r.dev_peak1 <= tol;
+    if (p2 >= 0) pass = pass && r.dev_peak2 <= tol;
+    r.pass = pass ? 1 : 0;
+    r.selected = pass ? candidate_storage : LBM_FP32;
+    if (report) *report = r;
+    return r.selected;
+}
+
+}  // extern "C"

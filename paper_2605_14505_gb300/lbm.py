@@ -75,6 +75,24 @@ class lbm_diag(ctypes.Structure):
         }
 
 
+class lbm_storage_report(ctypes.Structure):
+    _fields_ = [
+        ("dev_Ek", ctypes.c_double), ("dev_Ep", ctypes.c_double), ("dev_eps_k", ctypes.c_double),
+        ("dev_eps_p", ctypes.c_double), ("dev_peak1", ctypes.c_double), ("dev_peak2", ctypes.c_double),
+        ("step_peak1", ctypes.c_int64), ("step_peak2", ctypes.c_int64),
+        ("selected", ctypes.c_int32), ("pass_", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        names = {v: k for k, v in STORAGES.items()}
+        return {
+            "dev_Ek": self.dev_Ek, "dev_Ep": self.dev_Ep, "dev_eps_k": self.dev_eps_k,
+            "dev_eps_p": self.dev_eps_p, "dev_peak1": self.dev_peak1, "dev_peak2": self.dev_peak2,
+            "step_peak1": int(self.step_peak1), "step_peak2": int(self.step_peak2),
+            "selected": names.get(self.selected, self.selected), "pass": bool(self.pass_),
+        }
+
+
 _H = ctypes.c_void_p
 _DP = ctypes.POINTER(ctypes.c_double)
 _SIGS = {
@@ -102,6 +120,8 @@ _SIGS = {
     "lbm_prefetch_fields": ([_H, _DP, _DP, _DP], ctypes.c_int),
     "lbm_init_prefetched": ([_H], ctypes.c_int),
     "lbm_diagnostics_noalloc": ([_H, ctypes.POINTER(lbm_diag)], ctypes.c_int),
+    "lbm_storage_rule": ([ctypes.POINTER(lbm_diag), ctypes.POINTER(lbm_diag), ctypes.c_int64, ctypes.c_int,
+                          ctypes.c_double, ctypes.POINTER(lbm_storage_report)], ctypes.c_int),
     "lbm_get_fields": ([_H, _DP, _DP, _DP], ctypes.c_int),
     "lbm_get_populations": ([_H, _DP, _DP], ctypes.c_int),
     "lbm_set_populations": ([_H, _DP, _DP], ctypes.c_int),
@@ -308,6 +328,38 @@ def lbm_diagnostics_noalloc(h) -> dict:
     d = lbm_diag()
     _check(load_library().lbm_diagnostics_noalloc(h, ctypes.byref(d)))
     return d.as_dict()
+
+
+_DIAG_KEYS = ("Ek", "Ep", "eps_k", "eps_p", "eps_k_curl", "mass_f", "mass_g", "umax", "t", "Ek_phys",
+              "Ep_phys", "eps_k_phys", "eps_p_phys", "eps_k_curl_phys")
+
+
+def _diag_array(series):
+    """lbm_diag records from dicts (as returned by the diagnostics wrappers,
+    or by the oracle's view: missing fields are NaN)."""
+    arr = (lbm_diag * len(series))()
+    for rec, d in zip(arr, series):
+        for k in _DIAG_KEYS:
+            setattr(rec, k, float(d.get(k, float("nan"))))
+        for a, k in enumerate(("mom_x", "mom_y", "mom_z")):
+            rec.mom[a] = float(d.get(k, float("nan")))
+        rec.step = int(d["step"])
+    return arr
+
+
+def lbm_storage_rule(reference, candidate, candidate_storage, tol: float = 0.01) -> dict:
+    """The 16-bit storage rule of the C library on two diagnostics series
+    (lists of dicts with the same steps). Returns the report; report["selected"]
+    is the storage to use ("fp32" when the candidate misses the bound)."""
+    if len(reference) != len(candidate):
+        raise ValueError("the two series must have the same samples")
+    ref, cand = _diag_array(reference), _diag_array(candidate)
+    rep = lbm_storage_report()
+    rc = load_library().lbm_storage_rule(ref, cand, len(reference), _enum(candidate_storage, STORAGES),
+                                         float(tol), ctypes.byref(rep))
+    if rc < 0:
+        _check(rc)
+    return rep.as_dict()
 
 
 def lbm_get_fields(h, n3: int):
