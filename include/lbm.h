@@ -247,6 +247,13 @@ int lbm_step_diagnostics(lbm_handle h, int64_t nsteps, lbm_diag* out);
  * physical u (Eq. 7, 3 blocks), rho' (Eq. 16). Any pointer may be NULL. */
 int lbm_get_fields(lbm_handle h, double* rho, double* u, double* rho_p);
 
+/* The same fields written into caller-owned device memory (FP64, on the
+ * handle's device, the layout of lbm_get_fields; any pointer may be NULL),
+ * for post-processing on the GPU (e.g. the kinetic-energy spectrum of
+ * Section 3.5). Enqueued on the handle's stream; returns without waiting.
+ * LBM_EINVAL for a pointer that is not device memory of that device. */
+int lbm_get_fields_device(lbm_handle h, double* rho, double* u, double* rho_p);
+
 /* Full populations (not deviations) of the current state in FP64, host
  * arrays f[Q_f][n3], g[Q_g][n3], slot order of lbm_velocity_set. */
 int lbm_get_populations(lbm_handle h, double* f, double* g);
@@ -385,18 +392,25 @@ int lbm_destroy(lbm_handle h);
 /* ---- Batched instances -------------------------------------------------
  * A parameter sweep of the paper's kind (Sections 3.2-3.6: stencil pairs,
  * forcing schemes, Froude numbers, resolutions) as many independent periodic
- * lattices. Three drivers: per instance, each instance advanced by its own
- * single-lattice step kernel (its own launch shape), replayed from a CUDA
- * graph of 64 steps in which every instance's chain of steps is its own
- * branch (up to 128 branches, largest instances first; instances share no
- * memory, so the branches overlap and fill each other's tails); per step,
- * one launch per (pair, forcing) variant over that variant's tiles, replayed
- * the same way with one branch per variant; or one persistent cooperative
- * launch per `steps_per_launch` steps over all tiles with a bounded grid
- * barrier between steps. Instances may differ in size, pair (D3Q27xD3Q19,
- * D3Q19xD3Q7), forcing and parameters; storage is FP32. Each instance's
- * arithmetic is the single-lattice update's (bit for bit in the
- * per-instance driver, which runs the single-lattice kernels). */
+ * lattices. Three drivers:
+ *  - persistent (default): one launch advances every instance by
+ *    `steps_per_launch` steps. Each step's work is a list of tiles (runs of
+ *    consecutive nodes of one instance); blocks claim tiles from one queue in
+ *    step order, and a tile of step s starts once its own instance has
+ *    finished step s - 1 (a per-instance completion count), so instances never
+ *    wait for each other and there is no grid-wide barrier. Every wait is
+ *    bounded. The launch is replayed from a CUDA graph;
+ *  - per instance: each instance advanced by its own single-lattice step
+ *    kernel (its own launch shape), replayed from a CUDA graph of 64 steps in
+ *    which every instance's chain of steps is its own branch (up to 128
+ *    branches, largest instances first; instances share no memory, so the
+ *    branches overlap and fill each other's tails);
+ *  - per step: one launch per (pair, forcing) variant over that variant's
+ *    tiles, replayed the same way with one branch per variant.
+ * Instances may differ in size, pair (D3Q27xD3Q19, D3Q19xD3Q7), forcing and
+ * parameters; storage is FP32. Each instance's arithmetic is the
+ * single-lattice update's (bit for bit in the per-instance driver, which runs
+ * the single-lattice kernels). */
 typedef struct lbm_batch_ctx* lbm_batch;
 
 enum lbm_batch_mode { LBM_BATCH_PERSISTENT = 0, LBM_BATCH_PER_STEP = 1, LBM_BATCH_INSTANCES = 2 };
@@ -417,18 +431,25 @@ int lbm_batch_instance(lbm_batch b, int i, lbm_handle* h);
 /* Stream for all batch work (not owned; NULL disables graph replay). */
 int lbm_batch_set_stream(lbm_batch b, void* stream);
 
-/* LBM_BATCH_PERSISTENT (default; steps_per_launch steps per cooperative
- * launch, default 100), LBM_BATCH_PER_STEP (one launch per variant and step,
- * replayed from a CUDA graph of 64 steps) or LBM_BATCH_INSTANCES (each
+/* LBM_BATCH_PERSISTENT (default; steps_per_launch steps per persistent
+ * launch, default 100; at most 320 instances, whose descriptors travel in the
+ * launch's parameter block: LBM_EUNSUPPORTED beyond, and such batches start
+ * in LBM_BATCH_PER_STEP), LBM_BATCH_PER_STEP (one launch per variant and
+ * step, replayed from a CUDA graph of 64 steps) or LBM_BATCH_INSTANCES (each
  * instance's own step kernel, one graph branch per instance). */
 int lbm_batch_set_mode(lbm_batch b, int mode, int steps_per_launch);
 
-/* Tile shape: bx in {16, 32, 64, 128} nodes along x, by along y, bx*by a
- * multiple of 32 and <= 256 (default 32 x 8). */
+/* Tile shape of the per-step driver: bx in {16, 32, 64, 128} nodes along x,
+ * by along y, bx*by a multiple of 32 and <= 256 (default 32 x 8). */
 int lbm_batch_set_block(lbm_batch b, int bx, int by);
 
-/* Current tile shape, mode and grid size (blocks of the persistent launch,
- * or tiles for per-step launches). Pointers may be NULL. */
+/* Nodes per tile of the persistent driver: a multiple of 256 in
+ * [256, 65536] (default 2048; 256-thread blocks, nodes / 256 per thread). */
+int lbm_batch_set_flow_nodes(lbm_batch b, int nodes);
+int lbm_batch_get_flow_nodes(lbm_batch b, int* nodes);
+
+/* Current per-step tile shape, mode and grid size (blocks of the persistent
+ * launch, or tiles for per-step launches). Pointers may be NULL. */
 int lbm_batch_get_config(lbm_batch b, int* bx, int* by, int* mode, int* grid);
 
 /* lbm_init_tgv on every instance (same seed and noise amplitude). */
@@ -437,7 +458,7 @@ int lbm_batch_init_tgv(lbm_batch b, uint64_t seed, double noise_amp);
 /* Advance every instance by nsteps >= 0 steps, asynchronously. */
 int lbm_batch_step(lbm_batch b, int64_t nsteps);
 
-/* Wait for the batch stream. LBM_ETIMEOUT if a grid-barrier wait of a
+/* Wait for the batch stream. LBM_ETIMEOUT if a dependency wait of a
  * persistent launch ran out (the kernel then ended early and the instances'
  * state is undefined); the flag is cleared. */
 int lbm_batch_synchronize(lbm_batch b);
@@ -446,18 +467,21 @@ int lbm_batch_synchronize(lbm_batch b);
  * lbm_batch_synchronize; LBM_ENONFINITE if any instance has NaN/Inf). */
 int lbm_batch_diagnostics(lbm_batch b, lbm_diag* out);
 
-/* Time every tile shape under the per-step and persistent drivers, and the
- * per-instance driver after lbm_autotune of every instance's launch shape,
- * and keep the fastest: for each candidate one warm-up span, then reps spans
- * timed with CUDA events, a span being one 64-step graph (per-step and
- * per-instance drivers) or one persistent launch of steps_per_launch steps.
- * The instances' state is saved and restored. best_ms_per_step may be NULL. */
+/* Time the drivers and keep the fastest: every per-step tile shape, the
+ * persistent driver with 1024, 2048, 4096 and 8192 nodes per tile, and the
+ * per-instance driver after lbm_autotune of every instance's launch shape;
+ * for each candidate one warm-up span, then reps spans timed with CUDA
+ * events, a span being one 64-step graph (per-step and per-instance drivers)
+ * or one persistent launch of steps_per_launch steps. The instances' state is
+ * saved and restored. best_ms_per_step may be NULL. */
 int lbm_batch_autotune(lbm_batch b, int reps, double* best_ms_per_step);
 
-/* Fault-injection hook for tests of the timeout path: make each grid
- * barrier wait for `extra_blocks` arrivals that never come and give up after
- * `spin_limit` polls (default 0 and 4194304). */
-int lbm_batch_set_barrier_test(lbm_batch b, unsigned extra_blocks, unsigned spin_limit);
+/* Test hook for the timeout path of the persistent driver: every
+ * dependency wait expects `extra_completions` more completed tiles than
+ * exist (so with extra_completions > 0 the first wait of a launch's second
+ * step cannot complete) and gives up after `spin_limit` polls (defaults 0 and
+ * 4194304). */
+int lbm_batch_set_barrier_test(lbm_batch b, unsigned extra_completions, unsigned spin_limit);
 
 /* Free the batch, its instances and their stores. NULL is allowed. */
 int lbm_batch_destroy(lbm_batch b);

@@ -917,6 +917,36 @@ int lbm_get_fields(lbm_handle h, double* rho, double* u, double* rho_p)
     return LBM_OK;
 }
 
+int lbm_get_fields_device(lbm_handle h, double* rho, double* u, double* rho_p)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!h->initialized) return fail(LBM_ESTATE, "fields requested before initialisation");
+    double* outs[3] = {rho, u, rho_p};
+    for (double* p : outs) {
+        if (!p) continue;
+        cudaPointerAttributes attr;
+        cudaError_t e = cudaPointerGetAttributes(&attr, p);
+        if (e != cudaSuccess || attr.type != cudaMemoryTypeDevice || attr.device != h->device) {
+            cudaGetLastError();
+            return fail(LBM_EINVAL, "field outputs must be device memory on the handle's device");
+        }
+    }
+    FieldArgs a;
+    a.f = f_ptr(h);
+    a.g = g_ptr(h);
+    a.geo = h->geo;
+    a.ph = h->ph;
+    a.odd = h->odd;
+    a.rho = rho;
+    a.u = u;
+    a.rho_p = rho_p;
+    void* args[] = {&a};
+    LBM_CUDA(cudaLaunchKernel(h->ks->get_fields, dim3(flat_grid(h)), dim3(256), args, 0, h->stream),
+             "get_fields_device");
+    return LBM_OK;
+}
+
 int lbm_get_populations(lbm_handle h, double* f, double* g)
 {
     int rc = check_handle(h);
@@ -1330,7 +1360,17 @@ struct lbm_batch_ctx {
     int chunk = 100;
     int persistent_grid = 0;
     unsigned spin_limit = 1u << 22;   // ~0.3-1 s of polling at 64 ns naps
-    unsigned extra_blocks = 0;        // test hook: barrier arrivals that never come
+    unsigned extra_dep = 0;           // test hook: completions a dependency wait expects that never come
+    // persistent driver: one step's tile list, its tile size, the queue and
+    // completion counters, the kernel variant and its graphs (one per parity)
+    uint16_t* d_flow_inst = nullptr;
+    unsigned* d_flow = nullptr;
+    uint32_t flow_tiles = 0;
+    uint32_t flow_nodes = 2048;
+    bool guo_sc_only = false;
+    FlowArgs* flow_args = nullptr;   // the persistent launch's parameter block (descriptors by value)
+    cudaGraphExec_t pgraph[2] = {nullptr, nullptr};
+    int pgraph_steps[2] = {0, 0};
     bool initialized = false;
     int64_t step = 0;
     int odd = 0;
@@ -1346,6 +1386,11 @@ void batch_drop_graph(lbm_batch_ctx* b)
 {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
+    for (int k = 0; k < 2; ++k) {
+        if (b->pgraph[k]) cudaGraphExecDestroy(b->pgraph[k]);
+        b->pgraph[k] = nullptr;
+        b->pgraph_steps[k] = 0;
+    }
 }
 
 int batch_build_tiles(lbm_batch_ctx* b)
@@ -1380,12 +1425,40 @@ int batch_build_tiles(lbm_batch_ctx* b)
         b->vend[v] = t0;
     }
     b->ntiles = t0;
+    // persistent driver: runs of flow_nodes consecutive nodes, instances with
+    // the most bytes per step first
+    std::vector<size_t> big(b->inst.size());
+    for (size_t i = 0; i < big.size(); ++i) big[i] = i;
+    std::stable_sort(big.begin(), big.end(),
+                     [&](size_t a, size_t c) { return b->inst[a]->store_bytes > b->inst[c]->store_bytes; });
+    std::vector<uint16_t> flow;
+    b->guo_sc_only = true;
+    for (size_t i : big) {
+        BatchInstance& I = hi[i];
+        I.flow0 = (uint32_t)flow.size();
+        I.nflow = (I.geo.n3 + b->flow_nodes - 1) / b->flow_nodes;
+        flow.insert(flow.end(), (size_t)I.nflow, (uint16_t)i);
+        if (b->inst[i]->p.forcing != LBM_GUO && b->inst[i]->p.forcing != LBM_SHAN_CHEN) b->guo_sc_only = false;
+    }
+    if (flow.size() > 0x7fffffffull) return fail(LBM_EINVAL, "batch tile count exceeds 2^31");
+    b->flow_tiles = (uint32_t)flow.size();
+    if (hi.size() <= (size_t)kFlowMaxInst) {
+        if (!b->flow_args) b->flow_args = new (std::nothrow) FlowArgs();
+        if (!b->flow_args) return fail(LBM_ENOMEM, "host allocation failed");
+        for (size_t i = 0; i < hi.size(); ++i) b->flow_args->inst[i] = hi[i];
+    }
     if (b->d_inst) cudaFree(b->d_inst);
     if (b->d_tile) cudaFree(b->d_tile);
+    if (b->d_flow_inst) cudaFree(b->d_flow_inst);
+    if (b->d_flow) cudaFree(b->d_flow);
     b->d_inst = nullptr;
     b->d_tile = nullptr;
+    b->d_flow_inst = nullptr;
+    b->d_flow = nullptr;
     if (cudaMalloc(&b->d_inst, hi.size() * sizeof(BatchInstance)) != cudaSuccess ||
-        cudaMalloc(&b->d_tile, tiles.size() * sizeof(uint16_t)) != cudaSuccess) {
+        cudaMalloc(&b->d_tile, tiles.size() * sizeof(uint16_t)) != cudaSuccess ||
+        cudaMalloc(&b->d_flow_inst, flow.size() * sizeof(uint16_t)) != cudaSuccess ||
+        cudaMalloc(&b->d_flow, (1 + hi.size()) * sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
         return fail(LBM_ENOMEM, "batch descriptor allocation failed");
     }
@@ -1393,12 +1466,13 @@ int batch_build_tiles(lbm_batch_ctx* b)
              "copy batch descriptors");
     LBM_CUDA(cudaMemcpy(b->d_tile, tiles.data(), tiles.size() * sizeof(uint16_t), cudaMemcpyHostToDevice),
              "copy batch tiles");
+    LBM_CUDA(cudaMemcpy(b->d_flow_inst, flow.data(), flow.size() * sizeof(uint16_t), cudaMemcpyHostToDevice),
+             "copy batch tile list");
     int per_sm = 0;
-    LBM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persistent_kernel(), b->bx * b->by, 0),
+    LBM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_flow_kernel(b->guo_sc_only), 256, 0),
              "batch occupancy");
     if (per_sm < 1) return fail(LBM_EUNSUPPORTED, "persistent batch kernel does not fit on an SM");
-    uint64_t grid = (uint64_t)per_sm * (uint64_t)b->num_sms;
-    b->persistent_grid = (int)(grid < b->ntiles ? grid : b->ntiles);
+    b->persistent_grid = per_sm * b->num_sms;
     batch_drop_graph(b);
     return LBM_OK;
 }
@@ -1414,8 +1488,13 @@ BatchArgs batch_args(const lbm_batch_ctx* b, int steps, int odd0, unsigned grid)
     a.steps = steps;
     a.odd0 = odd0;
     a.sync = b->d_sync;
-    a.nblocks = grid + b->extra_blocks;
     a.spin_limit = b->spin_limit;
+    a.flow_inst = b->d_flow_inst;
+    a.flow_tiles = b->flow_tiles;
+    a.flow_nodes = b->flow_nodes;
+    a.flow = b->d_flow;
+    a.extra_dep = b->extra_dep;
+    (void)grid;
     return a;
 }
 
@@ -1504,12 +1583,40 @@ cudaError_t batch_capture_steps(lbm_batch_ctx* b, int steps)
     return e;
 }
 
+// One persistent launch of `steps` steps: clear the queue and completion
+// counters, then the kernel (a plain launch: see lbm_batch.cu).
 cudaError_t batch_launch_persistent(lbm_batch_ctx* b, int steps, int odd, cudaStream_t s)
 {
     const unsigned grid = (unsigned)b->persistent_grid;
-    BatchArgs a = batch_args(b, steps, odd, grid);
-    void* args[] = {&a};
-    return cudaLaunchCooperativeKernel(batch_persistent_kernel(), dim3(grid), dim3(b->bx, b->by), args, 0, s);
+    // the descriptors travel in the parameter block (b->flow_args, filled by
+    // batch_build_tiles); the launch copies it
+    FlowArgs& fa = *b->flow_args;
+    fa.a = batch_args(b, steps, odd, grid);
+    cudaError_t e = cudaMemsetAsync(b->d_flow, 0, (1 + b->inst.size()) * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    void* args[] = {&fa};
+    return cudaLaunchKernel(batch_flow_kernel(b->guo_sc_only), dim3(grid), dim3(256), args, 0, s);
+}
+
+// The same launch replayed from a CUDA graph (one per starting parity).
+cudaError_t batch_persistent_graph(lbm_batch_ctx* b, int steps, int odd)
+{
+    if (!b->pgraph[odd] || b->pgraph_steps[odd] != steps) {
+        if (b->pgraph[odd]) cudaGraphExecDestroy(b->pgraph[odd]);
+        b->pgraph[odd] = nullptr;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            e = batch_launch_persistent(b, steps, odd, b->stream);
+            cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->pgraph[odd], g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) return e;
+        b->pgraph_steps[odd] = steps;
+    }
+    return cudaGraphLaunch(b->pgraph[odd], b->stream);
 }
 
 void batch_sync_instances(lbm_batch_ctx* b)
@@ -1578,6 +1685,7 @@ int lbm_batch_create(lbm_batch* out, const lbm_params* params, int count)
         rc = fail(LBM_ENOMEM, "batch barrier allocation failed");
     }
     if (rc == LBM_OK) rc = batch_build_tiles(b);
+    if (rc == LBM_OK && b->inst.size() > (size_t)kFlowMaxInst) b->mode = LBM_BATCH_PER_STEP;
     if (rc) {
         std::string msg = g_last_error;
         lbm_batch_destroy(b);
@@ -1624,6 +1732,9 @@ int lbm_batch_set_mode(lbm_batch b, int mode, int steps_per_launch)
     if (mode != LBM_BATCH_PERSISTENT && mode != LBM_BATCH_PER_STEP && mode != LBM_BATCH_INSTANCES)
         return fail(LBM_EINVAL, "unknown mode %d", mode);
     if (steps_per_launch < 1) return fail(LBM_EINVAL, "steps per launch must be >= 1");
+    if (mode == LBM_BATCH_PERSISTENT && b->inst.size() > (size_t)kFlowMaxInst)
+        return fail(LBM_EUNSUPPORTED, "the persistent driver takes at most %d instances (batch has %zu)", kFlowMaxInst,
+                    b->inst.size());
     if (mode != b->mode) batch_drop_graph(b);   // the graph holds one driver's launches
     b->mode = mode;
     b->chunk = steps_per_launch;
@@ -1685,7 +1796,10 @@ int lbm_batch_step(lbm_batch b, int64_t nsteps)
     while (nsteps > 0) {
         if (b->mode == LBM_BATCH_PERSISTENT) {
             const int k = (int)(nsteps < b->chunk ? nsteps : b->chunk);
-            LBM_CUDA(batch_launch_persistent(b, k, b->odd, b->stream), "persistent batch launch");
+            if (b->stream != nullptr && k == b->chunk)
+                LBM_CUDA(batch_persistent_graph(b, k, b->odd), "persistent batch graph");
+            else
+                LBM_CUDA(batch_launch_persistent(b, k, b->odd, b->stream), "persistent batch launch");
             b->odd ^= (k & 1);
             b->step += k;
             nsteps -= k;
@@ -1727,7 +1841,7 @@ int lbm_batch_synchronize(lbm_batch b)
     LBM_CUDA(cudaMemcpy(flags, b->d_sync, sizeof(flags), cudaMemcpyDeviceToHost), "read barrier state");
     if (flags[2] != 0u) {
         cudaMemset(b->d_sync, 0, 4 * sizeof(unsigned));
-        return fail(LBM_ETIMEOUT, "a grid-barrier wait of the persistent batch kernel ran out; "
+        return fail(LBM_ETIMEOUT, "a dependency wait of the persistent batch kernel ran out; "
                                   "the state of the batch is undefined");
     }
     return LBM_OK;
@@ -1764,40 +1878,64 @@ int lbm_batch_autotune(lbm_batch b, int reps, double* best_ms_per_step)
         cudaMemcpyAsync(backup[i], b->inst[i]->store, b->inst[i]->store_bytes, cudaMemcpyDeviceToDevice, b->stream);
     }
     static const int cand[][2] = {{16, 8}, {32, 2}, {32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {128, 2}};
+    static const int flow_cand[] = {1024, 2048, 4096, 8192};
     const int save_bx = b->bx, save_by = b->by, save_mode = b->mode, save_odd = b->odd;
+    const uint32_t save_flow = b->flow_nodes;
     const int64_t save_step = b->step;
     double best = 1e300;
     int bbx = save_bx, bby = save_by, bmode = save_mode;
+    uint32_t bflow = save_flow;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    // one candidate as lbm_batch_step runs it: a warm-up span (which also
+    // builds the graphs), then `reps` spans timed with events; a span is one
+    // 64-step graph (per-step and per-instance drivers) or one persistent launch
+    auto time_mode = [&](int mode, double* per) {
+        b->mode = mode;
+        const int64_t span = (mode == LBM_BATCH_PERSISTENT) ? b->chunk : kBatchGraphSteps;
+        int r = lbm_batch_step(b, span);
+        if (r) return r;
+        cudaEventRecord(e0, b->stream);
+        r = lbm_batch_step(b, span * (int64_t)reps);
+        cudaEventRecord(e1, b->stream);
+        if (r) return r;
+        if ((r = lbm_batch_synchronize(b))) return r;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *per = ms / (double)(span * reps);
+        return LBM_OK;
+    };
     for (const auto& c : cand) {
         b->bx = c[0];
         b->by = c[1];
         if ((rc = batch_build_tiles(b))) break;
-        for (int mode = 0; mode < 2 && rc == LBM_OK; ++mode) {
-            // time whole graph chunks (per-step driver) and whole launches
-            // (persistent driver), as lbm_batch_step runs them
-            b->mode = mode;
-            const int64_t span = (mode == LBM_BATCH_PER_STEP) ? kBatchGraphSteps : b->chunk;
-            if ((rc = lbm_batch_step(b, span))) break;   // warm-up, builds the graph
-            cudaEventRecord(e0, b->stream);
-            rc = lbm_batch_step(b, span * (int64_t)reps);
-            cudaEventRecord(e1, b->stream);
-            if (rc) break;
-            if ((rc = lbm_batch_synchronize(b))) break;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            const double per = ms / (double)(span * reps);
-            if (per < best) {
-                best = per;
-                bbx = c[0];
-                bby = c[1];
-                bmode = mode;
-            }
+        double per = 0.0;
+        if ((rc = time_mode(LBM_BATCH_PER_STEP, &per))) break;
+        if (per < best) {
+            best = per;
+            bbx = c[0];
+            bby = c[1];
+            bmode = LBM_BATCH_PER_STEP;
         }
-        if (rc) break;
     }
+    b->bx = save_bx;
+    b->by = save_by;
+    const bool flow_ok = b->inst.size() <= (size_t)kFlowMaxInst;
+    for (size_t k = 0; flow_ok && k < sizeof(flow_cand) / sizeof(flow_cand[0]) && rc == LBM_OK; ++k) {
+        b->flow_nodes = (uint32_t)flow_cand[k];
+        if ((rc = batch_build_tiles(b))) break;
+        double per = 0.0;
+        if ((rc = time_mode(LBM_BATCH_PERSISTENT, &per))) break;
+        if (per < best) {
+            best = per;
+            bbx = save_bx;
+            bby = save_by;
+            bflow = b->flow_nodes;
+            bmode = LBM_BATCH_PERSISTENT;
+        }
+    }
+    b->flow_nodes = save_flow;
     if (rc == LBM_OK) {
         // per-instance driver: every instance's own launch shape, then whole
         // 64-step graphs of all chains
@@ -1821,6 +1959,7 @@ int lbm_batch_autotune(lbm_batch b, int reps, double* best_ms_per_step)
                 best = per;
                 bbx = b->bx;
                 bby = b->by;
+                bflow = b->flow_nodes;
                 bmode = LBM_BATCH_INSTANCES;
             }
         }
@@ -1836,6 +1975,7 @@ int lbm_batch_autotune(lbm_batch b, int reps, double* best_ms_per_step)
     b->step = save_step;
     b->bx = bbx;
     b->by = bby;
+    b->flow_nodes = bflow;
     b->mode = bmode;
     int rc2 = batch_build_tiles(b);
     batch_sync_instances(b);
@@ -1845,12 +1985,30 @@ int lbm_batch_autotune(lbm_batch b, int reps, double* best_ms_per_step)
     return LBM_OK;
 }
 
-int lbm_batch_set_barrier_test(lbm_batch b, unsigned extra_blocks, unsigned spin_limit)
+int lbm_batch_set_barrier_test(lbm_batch b, unsigned extra_completions, unsigned spin_limit)
 {
     if (!b) return fail(LBM_EINVAL, "null batch");
     if (spin_limit < 1) return fail(LBM_EINVAL, "spin limit must be >= 1");
-    b->extra_blocks = extra_blocks;
+    b->extra_dep = extra_completions;
     b->spin_limit = spin_limit;
+    batch_drop_graph(b);
+    return LBM_OK;
+}
+
+int lbm_batch_set_flow_nodes(lbm_batch b, int nodes)
+{
+    int rc = batch_check(b);
+    if (rc) return rc;
+    if (nodes < 256 || nodes > 65536 || nodes % 256 != 0)
+        return fail(LBM_EINVAL, "nodes per tile must be a multiple of 256 in [256, 65536] (got %d)", nodes);
+    b->flow_nodes = (uint32_t)nodes;
+    return batch_build_tiles(b);
+}
+
+int lbm_batch_get_flow_nodes(lbm_batch b, int* nodes)
+{
+    if (!b || !nodes) return fail(LBM_EINVAL, "null argument");
+    *nodes = (int)b->flow_nodes;
     return LBM_OK;
 }
 
@@ -1867,6 +2025,9 @@ int lbm_batch_destroy(lbm_batch b)
     }
     if (b->d_inst) cudaFree(b->d_inst);
     if (b->d_tile) cudaFree(b->d_tile);
+    if (b->d_flow_inst) cudaFree(b->d_flow_inst);
+    if (b->d_flow) cudaFree(b->d_flow);
+    delete b->flow_args;
     if (b->d_sync) cudaFree(b->d_sync);
     for (int v = 0; v < 8; ++v) {
         if (b->vstream[v]) cudaStreamDestroy(b->vstream[v]);

@@ -1,17 +1,28 @@
 // Batched update of many independent lattices (a parameter sweep over size,
-// Froude number, forcing scheme and stencil pair) in one launch.
+// Froude number, forcing scheme and stencil pair).
 //
-// The lattices are cut into tiles of blockDim.x x blockDim.y nodes of one
-// z-plane; one global tile list covers every instance. A block updates whole
-// tiles; the (pair, forcing) variant is uniform over a tile, so the switch
-// below never diverges inside a block. Two drivers:
-//   k_batch_variant     per time step one launch per (pair, forcing) variant over
-//                       that variant's tiles (graph-captured by the host);
-//   k_batch_persistent  a cooperative launch that advances `steps` time steps,
-//                       with a grid-wide barrier between steps. Every wait of
-//                       the barrier is bounded: after `spin_limit` polls the
-//                       block raises the error flag and returns, so a barrier
-//                       that cannot complete ends the kernel instead of hanging.
+// Two drivers live here:
+//   k_batch_variant  per time step one launch per (pair, forcing) variant
+//                    over that variant's tiles of bx x by nodes of one z-plane
+//                    (graph-captured by the host);
+//   k_batch_flow     one persistent launch that advances `steps` time steps
+//                    of every instance with no grid-wide barrier (below).
+//
+// k_batch_flow. Each step's work is one list of tiles, every instance cut
+// into runs of flow_nodes consecutive nodes (node index x + nx (y + ny z)).
+// Queue position q = s * flow_tiles + r stands for tile r of step s; blocks
+// claim positions from one global counter in increasing order, so every tile
+// of step s is claimed before any tile of step s + 1. Instances depend only
+// on themselves: a tile of instance i at step s > 0 starts once all nflow_i
+// tiles of instance i at step s - 1 are done (a per-instance completion
+// counter), because the AA step of a node reads and writes its neighbours'
+// slots. The next position is claimed while the current tile runs. A block
+// claims positions only while it is running, so whatever a block waits for
+// is held by running blocks that will finish it: the launch needs no
+// co-residency guarantee (a plain launch, capturable in a CUDA graph, of any
+// grid size). Every wait polls at most spin_limit times; a wait that runs out
+// raises the error flag, and any block that sees the flag stops, so the
+// kernel always ends.
 #include "lbm_dispatch.h"
 #include "lbm_kernels.cuh"
 
@@ -71,55 +82,94 @@ __global__ void __launch_bounds__(256, 3) k_batch_variant(BatchArgs A)
     }
 }
 
-// Grid-wide barrier for a cooperative launch. sync[0] counts arrivals,
-// sync[1] is the generation, sync[2] the error flag. Thread 0 of each block
-// reads the generation before arriving; the last block to arrive resets the
-// count and advances the generation. Returns false (after raising the flag)
-// if the generation did not move within spin_limit polls.
-__device__ __forceinline__ bool grid_barrier(const BatchArgs& A)
+// Nodes [n0, n1) of one instance, consecutive nodes on consecutive threads.
+template <class P, int FORCING, bool ODD>
+__device__ __forceinline__ void flow_nodes(const BatchInstance& I, uint32_t n0, uint32_t n1)
 {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        volatile unsigned* vsync = A.sync;
-        const unsigned gen = vsync[1];
-        int ok = 1;
-        __threadfence();
-        const unsigned arrived = atomicAdd(A.sync, 1u);
-        if (arrived == A.nblocks - 1) {
-            A.sync[0] = 0u;
-            __threadfence();
-            atomicAdd(A.sync + 1, 1u);
-        } else {
-            unsigned polls = 0;
-            while (vsync[1] == gen) {
-                if (++polls > A.spin_limit || vsync[2] != 0u) {
-                    atomicExch(A.sync + 2, 1u);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        s_ok = ok;
+    for (uint32_t n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+        int x, y, z;
+        node_xyz(I.geo, n, x, y, z);
+        batch_node<P, FORCING, ODD>(I, x, y, z);
     }
-    __syncthreads();
-    return s_ok != 0;
 }
 
-__global__ void __launch_bounds__(256) k_batch_persistent(BatchArgs A)
+// Variants compiled into a persistent kernel: bit v of MASK for variant v.
+constexpr int kFlowAll = 0xff;
+constexpr int kFlowGuoSC = 0x33;   // Guo and Shan-Chen on both pairs
+
+template <int MASK, bool ODD>
+__device__ __forceinline__ void flow_tile(const BatchInstance& I, uint32_t n0, uint32_t n1)
 {
-    int odd = A.odd0;
-    for (int s = 0; s < A.steps; ++s) {
-        for (uint32_t t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
-            if (odd)
-                batch_tile<true>(A, t);
-            else
-                batch_tile<false>(A, t);
+    switch (I.variant) {
+    case 0: if constexpr ((MASK & 1) != 0) flow_nodes<Pair<27, 19>, kGuo, ODD>(I, n0, n1); break;
+    case 1: if constexpr ((MASK & 2) != 0) flow_nodes<Pair<27, 19>, kShanChen, ODD>(I, n0, n1); break;
+    case 2: if constexpr ((MASK & 4) != 0) flow_nodes<Pair<27, 19>, kEDM, ODD>(I, n0, n1); break;
+    case 3: if constexpr ((MASK & 8) != 0) flow_nodes<Pair<27, 19>, kHCZ, ODD>(I, n0, n1); break;
+    case 4: if constexpr ((MASK & 16) != 0) flow_nodes<Pair<19, 7>, kGuo, ODD>(I, n0, n1); break;
+    case 5: if constexpr ((MASK & 32) != 0) flow_nodes<Pair<19, 7>, kShanChen, ODD>(I, n0, n1); break;
+    case 6: if constexpr ((MASK & 64) != 0) flow_nodes<Pair<19, 7>, kEDM, ODD>(I, n0, n1); break;
+    default: if constexpr ((MASK & 128) != 0) flow_nodes<Pair<19, 7>, kHCZ, ODD>(I, n0, n1); break;
+    }
+}
+
+// Thread 0: wait until `need` tiles of an instance are complete. False (with
+// the error flag raised) after spin_limit polls or once another block has
+// raised the flag.
+__device__ __forceinline__ bool flow_wait(const BatchArgs& A, uint32_t inst, uint32_t need)
+{
+    volatile unsigned* done = A.flow + 1 + inst;
+    volatile unsigned* flag = A.sync + 2;
+    unsigned polls = 0;
+    while (*done < need) {
+        if (++polls > A.spin_limit || *flag != 0u) {
+            atomicExch(A.sync + 2, 1u);
+            return false;
         }
-        if (s + 1 < A.steps && !grid_barrier(A)) return;
-        odd ^= 1;
+        __nanosleep(64);
+    }
+    __threadfence();   // acquire: the producers' stores are visible to this block after the barrier
+    return true;
+}
+
+static_assert(sizeof(FlowArgs) <= 32000, "persistent arguments within the kernel parameter limit");
+
+template <int MASK, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_batch_flow(const __grid_constant__ FlowArgs F)
+{
+    const BatchArgs& A = F.a;
+    __shared__ uint32_t s_q;
+    __shared__ int s_go;
+    const uint32_t total = (uint32_t)A.steps * A.flow_tiles;
+    uint32_t next = 0;   // thread 0: the position claimed for the next tile
+    if (threadIdx.x == 0) {
+        s_q = atomicAdd(A.flow, 1u);
+        next = atomicAdd(A.flow, 1u);
+    }
+    __syncthreads();
+    uint32_t q = s_q;
+    while (q < total) {
+        const uint32_t s = q / A.flow_tiles;
+        const uint32_t r = q - s * A.flow_tiles;
+        const uint32_t ii = A.flow_inst[r];
+        const BatchInstance& I = F.inst[ii];
+        if (threadIdx.x == 0) s_go = (s == 0) ? 1 : (int)flow_wait(A, ii, s * I.nflow + A.extra_dep);
+        __syncthreads();
+        if (!s_go) return;
+        const uint32_t n0 = (r - I.flow0) * A.flow_nodes;
+        const uint32_t n1 = min(n0 + A.flow_nodes, I.geo.n3);
+        if (((uint32_t)A.odd0 + s) & 1u)
+            flow_tile<MASK, true>(I, n0, n1);
+        else
+            flow_tile<MASK, false>(I, n0, n1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();   // release: this block's stores before the completion count
+            atomicAdd(A.flow + 1 + ii, 1u);
+            s_q = next;
+            if (next < total) next = atomicAdd(A.flow, 1u);
+        }
+        __syncthreads();
+        q = s_q;
     }
 }
 
@@ -143,6 +193,10 @@ const void* batch_variant_kernel(int variant, int odd)
     }
 }
 
-const void* batch_persistent_kernel() { return (const void*)k_batch_persistent; }
+// Guo / Shan-Chen only (80 registers, three blocks per SM as k_step), or every variant.
+const void* batch_flow_kernel(bool guo_sc_only)
+{
+    return guo_sc_only ? (const void*)k_batch_flow<kFlowGuoSC, 3> : (const void*)k_batch_flow<kFlowAll, 1>;
+}
 
 }  // namespace lbm

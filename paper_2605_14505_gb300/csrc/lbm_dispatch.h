@@ -32,6 +32,6 @@ const void* diag_final_kernel();
 
 // Batched update (FP32 storage, D3Q27xD3Q19 and D3Q19xD3Q7, all forcings).
 const void* batch_variant_kernel(int variant, int odd);   // variant = 4 * pair + forcing
-const void* batch_persistent_kernel();
+const void* batch_flow_kernel(bool guo_sc_only);   // persistent driver
 
 }  // namespace lbm

@@ -650,6 +650,8 @@ struct BatchInstance {
     int variant;      // 4 * (0: D3Q27xD3Q19, 1: D3Q19xD3Q7) + forcing
     uint32_t tile0;   // first tile of this instance in the global tile list
     uint32_t tx, ty;  // tiles along x and y of one z-plane
+    uint32_t flow0;   // persistent driver: first of its tiles in one step's list
+    uint32_t nflow;   // and their number (ceil(n3 / flow_nodes))
 };
 
 struct BatchArgs {
@@ -660,9 +662,24 @@ struct BatchArgs {
     uint32_t tile_end;
     int steps;                  // time steps of one persistent launch
     int odd0;                   // AA layout parity at the start
-    unsigned* sync;             // grid barrier: arrivals, generation, error flag
-    unsigned nblocks;           // blocks that must arrive at each barrier
-    unsigned spin_limit;        // polls before a barrier wait gives up
+    unsigned* sync;             // [2]: error flag raised by a wait that ran out
+    unsigned spin_limit;        // polls before a wait gives up
+    // persistent driver
+    const uint16_t* flow_inst;  // instance of every tile of one step's list
+    uint32_t flow_tiles;        // tiles in one step's list
+    uint32_t flow_nodes;        // nodes per tile (a multiple of the block size)
+    unsigned* flow;             // [0]: queue position counter; [1 + i]: tiles of instance i completed
+    unsigned extra_dep;         // test hook: completions every dependency wait expects beyond the real ones
+};
+
+// Persistent driver: the descriptors travel by value in the kernel's
+// parameter block (constant bank), like the single-lattice kernel's
+// arguments, so the per-node code reads them as constant loads that the
+// compiler can repeat instead of keeping ~18 values in registers.
+constexpr int kFlowMaxInst = 320;   // 320 * 96 bytes + the arguments stay under the 32 KB parameter limit
+struct FlowArgs {
+    BatchArgs a;
+    BatchInstance inst[kFlowMaxInst];
 };
 
 __device__ __forceinline__ void node_xyz(const Geometry& geo, uint32_t idx, int& x, int& y, int& z)
@@ -1134,11 +1151,13 @@ __global__ void k_get_fields(FieldArgs a)
             load_node<typename P::LG, false, T>(static_cast<const T*>(a.g), n3, na, k);
         }
         const Macro m = node_macro<P>(h, k, a.ph);
-        a.rho[idx] = (double)m.rho;
-        a.u[idx] = (double)m.ux;
-        a.u[(size_t)n3 + idx] = (double)m.uy;
-        a.u[2 * (size_t)n3 + idx] = (double)m.uz;
-        a.rho_p[idx] = (double)m.rho_p;
+        if (a.rho) a.rho[idx] = (double)m.rho;
+        if (a.u) {
+            a.u[idx] = (double)m.ux;
+            a.u[(size_t)n3 + idx] = (double)m.uy;
+            a.u[2 * (size_t)n3 + idx] = (double)m.uz;
+        }
+        if (a.rho_p) a.rho_p[idx] = (double)m.rho_p;
     }
 }
 

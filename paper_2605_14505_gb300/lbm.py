@@ -123,6 +123,7 @@ _SIGS = {
     "lbm_storage_rule": ([ctypes.POINTER(lbm_diag), ctypes.POINTER(lbm_diag), ctypes.c_int64, ctypes.c_int,
                           ctypes.c_double, ctypes.POINTER(lbm_storage_report)], ctypes.c_int),
     "lbm_get_fields": ([_H, _DP, _DP, _DP], ctypes.c_int),
+    "lbm_get_fields_device": ([_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "lbm_get_populations": ([_H, _DP, _DP], ctypes.c_int),
     "lbm_set_populations": ([_H, _DP, _DP], ctypes.c_int),
     "lbm_sample_populations": ([_H, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, _DP, _DP],
@@ -150,6 +151,8 @@ _SIGS = {
     "lbm_batch_diagnostics": ([_H, ctypes.POINTER(lbm_diag)], ctypes.c_int),
     "lbm_batch_autotune": ([_H, ctypes.c_int, _DP], ctypes.c_int),
     "lbm_batch_set_barrier_test": ([_H, ctypes.c_uint, ctypes.c_uint], ctypes.c_int),
+    "lbm_batch_set_flow_nodes": ([_H, ctypes.c_int], ctypes.c_int),
+    "lbm_batch_get_flow_nodes": ([_H, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "lbm_batch_destroy": ([_H], ctypes.c_int),
 }
 BATCH_MODES = {"persistent": 0, "per_step": 1, "instances": 2}
@@ -370,6 +373,12 @@ def lbm_get_fields(h, n3: int):
     return rho, u.reshape(3, n3), rho_p
 
 
+def lbm_get_fields_device(h, rho_ptr, u_ptr, rho_p_ptr):
+    """Device pointers (ints, or None) of FP64 buffers of n3, 3*n3, n3 values;
+    the fields are written asynchronously on the handle's stream."""
+    _check(load_library().lbm_get_fields_device(h, rho_ptr, u_ptr, rho_p_ptr))
+
+
 def lbm_get_populations(h, qf: int, qg: int, n3: int):
     f = np.empty(qf * n3)
     g = np.empty(qg * n3)
@@ -512,6 +521,18 @@ class Simulation:
     def fields(self):
         return lbm_get_fields(self.h, self.n3)
 
+    def fields_device(self):
+        """(rho, u[3, n3], rho') as FP64 CUDA tensors, written by the library
+        on its stream (which this waits for)."""
+        import torch
+
+        rho = torch.empty(self.n3, dtype=torch.float64, device="cuda")
+        u = torch.empty((3, self.n3), dtype=torch.float64, device="cuda")
+        rp = torch.empty(self.n3, dtype=torch.float64, device="cuda")
+        lbm_get_fields_device(self.h, rho.data_ptr(), u.data_ptr(), rp.data_ptr())
+        self.synchronize()
+        return rho, u, rp
+
     def populations(self):
         return lbm_get_populations(self.h, self.qf, self.qg, self.n3)
 
@@ -593,8 +614,18 @@ def lbm_batch_autotune(b, reps: int = 3) -> float:
     return ms.value
 
 
-def lbm_batch_set_barrier_test(b, extra_blocks: int, spin_limit: int):
-    _check(load_library().lbm_batch_set_barrier_test(b, extra_blocks, spin_limit))
+def lbm_batch_set_barrier_test(b, extra_completions: int, spin_limit: int):
+    _check(load_library().lbm_batch_set_barrier_test(b, extra_completions, spin_limit))
+
+
+def lbm_batch_set_flow_nodes(b, nodes: int):
+    _check(load_library().lbm_batch_set_flow_nodes(b, int(nodes)))
+
+
+def lbm_batch_get_flow_nodes(b) -> int:
+    n = ctypes.c_int()
+    _check(load_library().lbm_batch_get_flow_nodes(b, ctypes.byref(n)))
+    return n.value
 
 
 def lbm_batch_destroy(b):
