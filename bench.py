@@ -482,6 +482,116 @@ def run_ncu_case(args):
                       "sources": source_fingerprint()}))
 
 
+PAPER = {"n": 256, "pair": "27x19", "forcing": "sc", "Re": 1600.0, "Sc": 0.7, "U0": 0.0577}
+FROUDE = (1.0, 0.1, 0.3, 0.5, 0.9, 1.5, 2.5)
+X1_RE = (100.0, 200.0, 400.0, 800.0, 1600.0, 3000.0)
+X1_U0 = 0.05 / 3 ** 0.5   # Ma 0.05 (Section 3.1)
+
+
+def paper_series(n, pair, forcing, Re, Fr, Sc, U0, t_end, storage="fp32", seed=1, noise_amp=0.0,
+                 spectrum_at=None, every_tc=0.1):
+    """Diagnostics every ~every_tc convective times to t_end (lbm_step_diagnostics:
+    reduced inside the step kernel), and optionally the kinetic-energy spectrum of
+    the first sample at t >= spectrum_at (fields written to device memory, cuFFT)."""
+    from paper_2605_14505_gb300 import lbm, post
+
+    p = lbm.lbm_params_from_physics(n, n, n, pair, forcing, Re, Fr, Sc, U0)
+    sim = lbm.Simulation(p, storage=storage)
+    sim.init_tgv(seed=seed, noise_amp=noise_amp)
+    steps_tc = p.L / U0
+    every = max(1, round(every_tc * steps_tc))
+    total = round(t_end * steps_tc)
+    series, spec = [], None
+    t0 = time.perf_counter()
+    while sim.step_count <= total:
+        if spectrum_at is not None and spec is None and sim.step_count * U0 / p.L >= spectrum_at:
+            _, u, _ = sim.fields_device()
+            k, E = post.energy_spectrum_device(u, n)
+            spec = {"t": sim.step_count * U0 / p.L, "k": k.tolist(), "E_phys": (E / U0 ** 2).tolist()}
+        series.append(sim.step_diagnostics(every, allow_nonfinite=True))
+        if not all(map(lambda v: v == v, (series[-1]["Ek"], series[-1]["eps_k"]))):
+            break
+    sim.synchronize()
+    secs = time.perf_counter() - t0
+    sim.close()
+    return series, spec, secs
+
+
+def run_validation(args):
+    """The paper's own runs at 256^3 on one GPU (context, not gates: the paper's
+    DNS references are not available):
+      - X1 (Section 3.1): the unstratified TGV (G = 0), D3Q27, Ma 0.05, Re in
+        {100, ..., 3000}: eps = -dE_k/dt (central differences) against the
+        non-equilibrium eps_k in the laminar window t in [0.5, 3], and the
+        peak of -dE_k/dt;
+      - the Froude sweep (Sections 3.3-3.5): Re0 1600, Sc 0.7, Ma 0.1, D3Q27xD3Q19,
+        Shan-Chen, Fr0 in {1, 0.1, 0.3, 0.5, 0.9, 1.5, 2.5} to t = 30: the two
+        highest peaks of the total dissipation -dE_tot/dt, the peaks of R (Eq. 27)
+        and Gamma, Gamma_b (Eq. 28), Fr_t (Eq. 29) and the spectral slope at t = 15;
+      - the 16-bit storage rule in the double-peak regime (Fr0 = 1): FP16 and BF16
+        against the FP32 run, beside an FP32 twin whose initial field differs by
+        1e-6 U0 noise (the spread of the flow's own sensitivity)."""
+    import numpy as np
+
+    from paper_2605_14505_gb300 import lbm, post
+
+    out = {"mode": "validation", "lattice": 256}
+    todo = set(args.validation.split(",")) if args.validation != "all" else {"x1", "froude", "storage"}
+    if "x1" in todo:
+        x1 = {}
+        for Re in X1_RE:
+            ser, _, secs = paper_series(256, "27x19", "guo", Re, float("inf"), 1.0, X1_U0, args.x1_tend)
+            ph = post.to_physical(ser)
+            rate = post.total_dissipation_rate(ph["t"], ph["Ek"])
+            m = (ph["t"] >= 0.5) & (ph["t"] <= 3.0)
+            pk = post.peaks(ph["t"], rate, 1)
+            x1[str(int(Re))] = {
+                "laminar_max_rel_diff": float(np.max(np.abs(rate[m] / ph["eps_k"][m] - 1))),
+                "peak_t": pk[0][0] if pk else None, "peak_eps": pk[0][1] if pk else None,
+                "finite": bool(np.all(np.isfinite(ph["Ek"]))), "samples": len(ser), "secs": round(secs, 1)}
+            print("x1", Re, x1[str(int(Re))], file=sys.stderr, flush=True)
+        out["x1"] = x1
+    if "froude" in todo or "storage" in todo:
+        fr_out, ref_series = {}, None
+        for Fr in (FROUDE if "froude" in todo else (1.0,)):
+            ser, spec, secs = paper_series(PAPER["n"], PAPER["pair"], PAPER["forcing"], PAPER["Re"], Fr, PAPER["Sc"],
+                                           PAPER["U0"], 30.0, spectrum_at=15.0)
+            if Fr == 1.0:
+                ref_series = ser
+            ph = post.to_physical(ser)
+            t = ph["t"]
+            rate = post.total_dissipation_rate(t, ph["Etot"])
+            R = post.buoyancy_reynolds(ph["eps_k"], PAPER["Re"], Fr)
+            gam = post.flux_coefficient(ph["eps_p"], ph["eps_k"])
+            rec = {"dissipation_peaks": post.peaks(t, rate, 2), "eps_sum_peaks": post.peaks(t, ph["eps_k"] + ph["eps_p"], 2),
+                   "R_peaks": post.peaks(t, R, 2), "Gamma_max": [float(t[np.argmax(gam[1:]) + 1]), float(np.max(gam[1:]))],
+                   "Gamma_b": float(post.bulk_flux_coefficient(t, ph["eps_p"], ph["eps_k"])),
+                   "Fr_t": float(post.turbulent_froude(t, ph["eps_k"], ph["Ek"], Fr)),
+                   "Ek_end": float(ph["Ek"][-1]), "Ep_max": float(np.max(ph["Ep"])),
+                   "finite": bool(np.all(np.isfinite(ph["Ek"]))), "samples": len(ser), "secs": round(secs, 1)}
+            if spec:
+                rec["spectrum_t"] = spec["t"]
+                rec["spectral_slope_k4_20"] = post.spectral_slope(spec["k"], spec["E_phys"], 4, 20)
+                rec["E_k_spectrum"] = [float(f"{v:.4e}") for v in spec["E_phys"][:65]]
+            fr_out[str(Fr)] = rec
+            print("froude", Fr, {k: v for k, v in rec.items() if k != "E_k_spectrum"}, file=sys.stderr, flush=True)
+        if "froude" in todo:
+            out["froude_sweep"] = fr_out
+        if "storage" in todo:
+            st = {}
+            twin, _, _ = paper_series(PAPER["n"], PAPER["pair"], PAPER["forcing"], PAPER["Re"], 1.0, PAPER["Sc"],
+                                      PAPER["U0"], 30.0, seed=7, noise_amp=1e-6)
+            st["fp32_twin_1e-6"] = lbm.lbm_storage_rule(ref_series, twin, "fp32", 0.01)
+            for storage in ("fp16", "bf16"):
+                ser, _, secs = paper_series(PAPER["n"], PAPER["pair"], PAPER["forcing"], PAPER["Re"], 1.0, PAPER["Sc"],
+                                            PAPER["U0"], 30.0, storage=storage)
+                st[storage] = lbm.lbm_storage_rule(ref_series, ser, storage, 0.01)
+                st[storage]["secs"] = round(secs, 1)
+            out["storage_rule_fr1"] = st
+            print("storage", st, file=sys.stderr, flush=True)
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -502,8 +612,14 @@ def main():
                     help="profiling case: nodes per thread for 16-bit storage (lbm_set_pairing)")
     ap.add_argument("--ncu-staging", action="store_true",
                     help="profiling case: bulk-copy tile staging for 16-bit storage (lbm_set_tile_staging)")
+    ap.add_argument("--validation", default=None,
+                    help="run the paper's validation runs instead of the benchmark: all, or a comma list of "
+                         "x1, froude, storage")
+    ap.add_argument("--x1-tend", type=float, default=14.0, help="end time of the unstratified runs")
     args = ap.parse_args()
-    if args.ncu_case:
+    if args.validation:
+        run_validation(args)
+    elif args.ncu_case:
         run_ncu_case(args)
     elif args.impl == "reference":
         run_reference_arm(args)

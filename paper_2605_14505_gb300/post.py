@@ -90,3 +90,38 @@ def energy_spectrum(u, n: int):
     shell = np.rint(np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2)).astype(np.int64)
     E = np.bincount(shell.ravel(), weights=e.ravel())
     return np.arange(len(E)), E
+
+
+def energy_spectrum_device(u, n: int):
+    """energy_spectrum on the GPU: u is a CUDA tensor (3, n^3), x fastest. The
+    3-D FFT is cuFFT through torch.fft (a library transform off the update
+    path); the shells are summed with one bincount. Returns numpy (k, E)."""
+    import torch
+
+    uh = torch.fft.fftn(u.reshape(3, n, n, n), dim=(1, 2, 3)) / n ** 3
+    e = 0.5 * (uh.real ** 2 + uh.imag ** 2).sum(dim=0)
+    kk = torch.fft.fftfreq(n, d=1.0 / n, device=u.device, dtype=torch.float64)
+    KZ, KY, KX = torch.meshgrid(kk, kk, kk, indexing="ij")
+    shell = torch.round(torch.sqrt(KX ** 2 + KY ** 2 + KZ ** 2)).to(torch.int64)
+    E = torch.bincount(shell.flatten(), weights=e.flatten())
+    E = E.cpu().numpy()
+    return np.arange(len(E)), E
+
+
+def spectral_slope(k, E, kmin: float, kmax: float) -> float:
+    """Least-squares slope of log E against log k over kmin <= k <= kmax
+    (the paper compares the inertial range with k^(-5/3), Section 3.5)."""
+    k = np.asarray(k, dtype=np.float64)
+    E = np.asarray(E, dtype=np.float64)
+    m = (k >= kmin) & (k <= kmax) & (E > 0)
+    return float(np.polyfit(np.log(k[m]), np.log(E[m]), 1)[0])
+
+
+def peaks(t, y, count: int = 2):
+    """The `count` highest interior local maxima of a sampled series, as
+    (t, y) pairs in time order."""
+    t = np.asarray(t, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    idx = [i for i in range(1, len(y) - 1) if y[i] > y[i - 1] and y[i] >= y[i + 1]]
+    idx = sorted(sorted(idx, key=lambda i: -y[i])[:count])
+    return [(float(t[i]), float(y[i])) for i in idx]

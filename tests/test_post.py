@@ -49,3 +49,12 @@ def test_spectrum_of_the_taylor_green_field():
     k, E = post.energy_spectrum(u, n)
     assert abs(E.sum() - 0.5 * np.mean(np.sum(u ** 2, axis=0))) < 1e-12
     assert abs(E[2] - 0.125) < 1e-12 and abs(E.sum() - E[2]) < 1e-12
+
+
+def test_spectral_slope_and_peaks():
+    k = np.arange(1, 40, dtype=float)
+    assert abs(post.spectral_slope(k, 3.0 * k ** (-5.0 / 3.0), 4, 20) + 5.0 / 3.0) < 1e-12
+    t = np.linspace(0, 20, 401)
+    y = np.exp(-((t - 11.5) / 1.0) ** 2) + 0.8 * np.exp(-((t - 16.5) / 1.0) ** 2) + 0.3 * np.exp(-((t - 3) / 0.5) ** 2)
+    p = post.peaks(t, y, 2)
+    assert [round(a, 2) for a, _ in p] == [11.5, 16.5]
