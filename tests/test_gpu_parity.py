@@ -568,3 +568,49 @@ def test_field_initialisation_rounds_fp64_fields_to_nearest_even():
     assert np.array_equal(f0[k:2 * k].view(np.uint32), exp_u.view(np.uint32))
     assert np.array_equal(g0[2 * k:3 * k].view(np.uint32), exp_rp.view(np.uint32))
     s.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_device_fields_equal_host_fields(storage):
+    """lbm_get_fields_device writes the same FP64 fields as lbm_get_fields
+    (after an odd step count, so the swapped AA arrangement is read)."""
+    import torch
+
+    n = 24
+    p = lbm.lbm_params_from_physics(n, n, n, "27x19", "sc", 100.0, 0.5, 1.0, 0.04)
+    s = gpu_sim(p, storage)
+    s.init_tgv(seed=3, noise_amp=0.01)
+    s.step(7)
+    rho, u, rp = s.fields()
+    drho, du, drp = s.fields_device()
+    assert np.array_equal(drho.cpu().numpy(), rho)
+    assert np.array_equal(du.cpu().numpy(), u)
+    assert np.array_equal(drp.cpu().numpy(), rp)
+    # one output only; a host pointer is rejected
+    only_u = torch.zeros((3, n ** 3), dtype=torch.float64, device="cuda")
+    lbm.lbm_get_fields_device(s.h, None, only_u.data_ptr(), None)
+    s.synchronize()
+    assert np.array_equal(only_u.cpu().numpy(), u)
+    host = np.zeros(n ** 3)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_get_fields_device(s.h, host.ctypes.data, None, None)
+    assert ei.value.code == -1
+    s.close()
+
+
+def test_gpu_spectrum_matches_host_spectrum():
+    """The cuFFT spectrum of the device field equals the numpy one."""
+    from paper_2605_14505_gb300 import post
+
+    n = 32
+    p = lbm.lbm_params_from_physics(n, n, n, "27x19", "sc", 400.0, 1.0, 0.7, 0.0577)
+    s = gpu_sim(p)
+    s.init_tgv(seed=1, noise_amp=0.01)
+    s.step(50)
+    _, u, _ = s.fields()
+    _, du, _ = s.fields_device()
+    k1, E1 = post.energy_spectrum(u, n)
+    k2, E2 = post.energy_spectrum_device(du, n)
+    assert np.array_equal(k1, k2)
+    assert np.allclose(E1, E2, rtol=1e-10, atol=1e-22)
+    s.close()
