@@ -259,10 +259,19 @@ def run_gpu_arm(args):
             "roofline": {"bound": "hbm", "achieved": round(vach, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(vach / peak, 4), "traffic": ncu_traffic(storage),
                          "algorithmic_bytes_per_launch": bytes_per_node(storage) * n3},
-            "rel_dev_vs_fp32_gpu": {k: float(f"{v:.3e}") for k, v in err.items()},
+            "rel_dev_vs_fp32_gpu_at_last_timed_step": {k: float(f"{v:.3e}") for k, v in err.items()},
             "bytes_per_node": bytes_per_node(storage),
         }
         s.close()
+
+    # the 16-bit storage rule (lbm_storage_rule, <= 1 % on E_k, E_p, eps_k,
+    # eps_p and the two eps peaks, else FP32) on whole series: against the
+    # stored FP64 oracle series of the 64^3 runs, and on this workload's full
+    # 20000 steps against its FP32 run (no oracle at 256^3)
+    if not args.no_series:
+        precision = storage_rule_series(args)
+        for storage in ("fp16", "bf16"):
+            variants[storage]["storage_rule"] = precision[storage]
 
     # end to end through the C ABI with host buffers: every bench step sets the
     # lattice from FP64 fields in pinned host memory, advances 100 steps and
@@ -297,7 +306,7 @@ def run_gpu_arm(args):
     e2e = {"value": round(aggregate_mlups(float(n3) * DIAG_EVERY * args.steps, world, e2e_secs), 1),
            "unit": "MLUPS", "h2d_bytes_per_step": 5 * n3 * 8, "d2h_bytes_per_step": 11 * 8}
 
-    batch = run_batch_sweep(args, peak) if not args.no_batch else None
+    batch = run_batch_sweep(args, peak, world, rank) if not args.no_batch else None
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
@@ -330,6 +339,71 @@ def run_gpu_arm(args):
         dist.destroy_process_group()
 
 
+SERIES_STEPS, SERIES_EVERY = 20000, 100
+
+
+def _series(n, pair, forcing, Re, Fr, Sc, U0_, steps, every, seed, amp, storage, host_fields):
+    """Diagnostics every `every` steps (lbm_step_diagnostics) from step 0 to `steps`."""
+    import stgv_inputs as inputs
+    from paper_2605_14505_gb300 import lbm
+
+    p = lbm.lbm_params_from_physics(n, n, n, pair, forcing, Re, Fr, Sc, U0_)
+    sim = lbm.Simulation(p, storage=storage)
+    if host_fields:
+        sim.init_fields(*inputs.tgv_fields(n, U0_, seed=seed, noise_amp=amp))
+    else:
+        sim.init_tgv(seed=seed, noise_amp=amp)
+    out = [sim.step_diagnostics(every, allow_nonfinite=True) for _ in range(steps // every)]
+    out.append(sim.diagnostics(allow_nonfinite=True))
+    sim.close()
+    return out
+
+
+def storage_rule_series(args) -> dict:
+    """FP16 and BF16 deviation storage judged by the library's storage rule:
+      - against the FP64 oracle: the stored oracle series of two 64^3 runs
+        (written by tests/golden/make_oracle_series.py; no oracle code runs
+        here): Re 200 / Fr 0.1 (laminar) and the paper's Re0 1600 / Fr0 1
+        (turbulent breakdown, t ~ 30);
+      - on the 256^3 workload's full 20000 steps (diagnostics every 100)
+        against the FP32-storage run on this GPU."""
+    import importlib.util
+
+    from paper_2605_14505_gb300 import lbm
+
+    spec = importlib.util.spec_from_file_location(
+        "make_oracle_series", os.path.join(ROOT, "tests", "golden", "make_oracle_series.py"))
+    G = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(G)
+    keys = ("dev_Ek", "dev_Ep", "dev_eps_k", "dev_eps_p", "dev_peak1", "dev_peak2")
+
+    def brief(rep):
+        d = {k: float(f"{rep[k]:.3e}") for k in keys}
+        d.update(selected=rep["selected"], step_peak1=rep["step_peak1"], step_peak2=rep["step_peak2"])
+        return d
+
+    res = {"fp16": {}, "bf16": {}}
+    for name in G.SERIES:
+        n, (qf, qg), forcing, Re, Fr, Sc, U0_, steps, every, seed, amp = G.SERIES[name]
+        ref = G.read(name)
+        for storage in res:
+            got = _series(n, f"{qf}x{qg}", forcing, Re, Fr, Sc, U0_, steps, every, seed, amp, storage, True)
+            for d, r in zip(got, ref):
+                assert d["step"] == r["step"]
+            res[storage]["vs_fp64_oracle_" + name] = brief(lbm.lbm_storage_rule(ref, got, storage, 0.01))
+    if args.series_steps > 0:
+        ref = _series(N, PAIR, FORCING, RE, FR, PR, U0, args.series_steps, SERIES_EVERY, 1, 1e-3, "fp32", False)
+        for storage in res:
+            got = _series(N, PAIR, FORCING, RE, FR, PR, U0, args.series_steps, SERIES_EVERY, 1, 1e-3, storage, False)
+            rep = brief(lbm.lbm_storage_rule(ref, got, storage, 0.01))
+            rep["steps"] = args.series_steps
+            res[storage]["vs_fp32_gpu_256cubed_workload"] = rep
+    for storage in res:
+        res[storage]["verdict"] = "kept" if all(v["selected"] == storage for v in res[storage].values()) \
+            else "fp32 fallback"
+    return res
+
+
 SWEEP_STEPS = 2000
 
 
@@ -340,47 +414,60 @@ def sweep_specs():
             for forcing in ("guo", "sc") for pair in ("19x7", "27x19")]
 
 
-def run_batch_sweep(args, peak):
-    """All 64 instances advanced together for 2000 steps (graph-replayed
-    per-variant launches or persistent cooperative launches, tile shape and
-    driver picked by the library's autotuner). Aggregate MLUPS and the HBM
-    roofline fraction of the whole batch."""
+def run_batch_sweep(args, peak, world=1, rank=0):
+    """The 64 instances advanced together for 2000 steps, driver and launch
+    shapes picked by the library's autotuner. Aggregate MLUPS and the HBM
+    roofline fraction of the whole batch. Under torchrun the instances are
+    split over the ranks by lbm_batch_partition (bytes per step, longest
+    first): each rank advances only its own, with no lattice data exchanged,
+    and the job's time is the slowest rank's (the sweep's total work is fixed:
+    strong scaling)."""
     import numpy as np
     import torch
 
     from paper_2605_14505_gb300 import lbm
 
     specs = sweep_specs()
-    params = [lbm.lbm_params_from_physics(n, n, n, pair, f, Re, Fr, 1.0, U0) for n, pair, f, Re, Fr in specs]
+    params_all = [lbm.lbm_params_from_physics(n, n, n, pair, f, Re, Fr, 1.0, U0) for n, pair, f, Re, Fr in specs]
+    owner, imbalance = lbm.lbm_batch_partition(params_all, world)
+    mine = [i for i in range(len(specs)) if owner[i] == rank]
+    params = [params_all[i] for i in mine]
     b = lbm.lbm_batch_create(params)
     lbm.lbm_batch_init_tgv(b, seed=1, noise_amp=1e-3)
     tuned_ms = lbm.lbm_batch_autotune(b, 3)
     cfg = lbm.lbm_batch_get_config(b)
+    flow_nodes = lbm.lbm_batch_get_flow_nodes(b)
     lbm.lbm_batch_step(b, 100)
     lbm.lbm_batch_synchronize(b)
+    barrier(world)
     t = time.perf_counter()
     steps = args.sweep_steps
     lbm.lbm_batch_step(b, steps)
     lbm.lbm_batch_synchronize(b)
-    secs = time.perf_counter() - t
+    secs = max_over_ranks(world, time.perf_counter() - t)
     nodes = sum(n ** 3 for n, *_ in specs)
     nbytes = sum(n ** 3 * (bytes_per_node("fp32") if pair == "27x19" else (19 + 7) * 2 * 4)
                  for n, pair, *_ in specs)
     diags = lbm.lbm_batch_diagnostics(b)
     lbm.lbm_batch_destroy(b)
     torch.cuda.synchronize()
+    finite = all(np.isfinite(d["Ek"]) for d in diags)
+    if world > 1:
+        finite = max_over_ranks(world, 0.0 if finite else 1.0) == 0.0
     achieved = nbytes * steps / secs / 1e9
+    drivers = {0: "persistent", 1: "per_step", 2: "instances"}
     return {"instances": len(specs), "nodes": nodes, "steps": steps,
             "mlups": round(nodes * steps / secs / 1e6, 1), "ms_per_step": round(secs * 1e3 / steps, 4),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "bytes_per_step": nbytes},
-            **({"driver": "instances", "launch_shapes": "per instance (autotuned)"} if cfg["mode"] == 2 else
-               {"driver": "persistent" if cfg["mode"] == 0 else "per_step", "tile": [cfg["bx"], cfg["by"]],
-                ("grid" if cfg["mode"] == 0 else "tiles"): cfg["grid"]}),
+                         "frac": round(achieved / peak / world, 4), "bytes_per_step": nbytes,
+                         "counts": "algorithmic bytes (every population read and written once per step)"},
+            "driver": drivers[cfg["mode"]],
+            "tile": [cfg["bx"], cfg["by"]] if cfg["mode"] == 1 else None,
+            "flow_nodes": flow_nodes if cfg["mode"] == 0 else None,
             "autotune_ms_per_step": round(tuned_ms, 4),
-            "l2": "achieved counts algorithmic bytes; the per-instance driver runs each instance's steps back "
-                  "to back, so the 32^3-48^3 instances (12-40 MB) are partly served from L2 between steps",
-            "all_finite": all(np.isfinite(d["Ek"]) for d in diags), "timing": f"host wall clock around {steps} steps"}
+            "ranks": world, "instances_this_rank": len(mine), "partition_imbalance": round(imbalance, 4),
+            "scaling": "strong (the 64 instances split over the ranks)" if world > 1 else None,
+            "all_finite": finite, "timing": f"host wall clock around {steps} steps, max over ranks"}
 
 
 def cpu_baseline(steps: int = 2) -> dict:
@@ -601,6 +688,10 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched sweep")
+    ap.add_argument("--no-series", action="store_true",
+                    help="skip the storage-rule series (64^3 against the stored oracle series, 256^3 workload)")
+    ap.add_argument("--series-steps", type=int, default=SERIES_STEPS,
+                    help="steps of the 256^3 workload series for the storage rule (0: skip it)")
     ap.add_argument("--sweep-steps", type=int, default=SWEEP_STEPS,
                     help="timed steps of the batched sweep (fewer for a bounded profiler launch list)")
     ap.add_argument("--ncu-case", choices=["fp32", "fp16", "bf16", "19x7", "19x7-fp16", "batch", "batch-step"],

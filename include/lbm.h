@@ -483,6 +483,17 @@ int lbm_batch_autotune(lbm_batch b, int reps, double* best_ms_per_step);
  * 4194304). */
 int lbm_batch_set_barrier_test(lbm_batch b, unsigned extra_completions, unsigned spin_limit);
 
+/* Split a sweep of independent instances over nranks processes, one GPU
+ * each, with no communication on the data path: every rank computes the same
+ * owner table and creates a batch of the instances it owns. Longest
+ * processing time first: instances in decreasing order of bytes per step
+ * ((Q_f + Q_g) * nx*ny*nz * element size; ties by lower index), each to the
+ * rank with the fewest bytes so far (ties: lower rank). owner[count]
+ * receives each instance's rank; *imbalance (may be NULL) the largest rank's
+ * bytes over the mean. Host-only: no device work. LBM_EINVAL for bad
+ * arguments or parameters. */
+int lbm_batch_partition(const lbm_params* params, int count, int nranks, int32_t* owner, double* imbalance);
+
 /* Free the batch, its instances and their stores. NULL is allowed. */
 int lbm_batch_destroy(lbm_batch b);
 

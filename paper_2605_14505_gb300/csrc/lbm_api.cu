@@ -1995,6 +1995,41 @@ int lbm_batch_set_barrier_test(lbm_batch b, unsigned extra_completions, unsigned
     return LBM_OK;
 }
 
+int lbm_batch_partition(const lbm_params* params, int count, int nranks, int32_t* owner, double* imbalance)
+{
+    if (!params || !owner || count < 1 || count > 65535 || nranks < 1)
+        return fail(LBM_EINVAL, "lbm_batch_partition: null argument, count outside [1, 65535] or nranks < 1");
+    std::vector<double> bytes(count);
+    for (int i = 0; i < count; ++i) {
+        PairInfo q;
+        int rc = validate_params(&params[i], &q);
+        if (rc) return rc;
+        bytes[i] = (double)(q.qf + q.qg) * (double)params[i].nx * params[i].ny * params[i].nz *
+                   (double)elem_size(params[i].storage);
+    }
+    // longest first (ties: lower index first), each to the least-loaded rank (ties: lower rank)
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return bytes[a] > bytes[c]; });
+    std::vector<double> load(nranks, 0.0);
+    for (int i : order) {
+        int r = 0;
+        for (int k = 1; k < nranks; ++k)
+            if (load[k] < load[r]) r = k;
+        owner[i] = r;
+        load[r] += bytes[i];
+    }
+    if (imbalance) {
+        double total = 0.0, mx = 0.0;
+        for (double l : load) {
+            total += l;
+            mx = std::max(mx, l);
+        }
+        *imbalance = mx / (total / nranks);
+    }
+    return LBM_OK;
+}
+
 int lbm_batch_set_flow_nodes(lbm_batch b, int nodes)
 {
     int rc = batch_check(b);

@@ -152,6 +152,8 @@ _SIGS = {
     "lbm_batch_autotune": ([_H, ctypes.c_int, _DP], ctypes.c_int),
     "lbm_batch_set_barrier_test": ([_H, ctypes.c_uint, ctypes.c_uint], ctypes.c_int),
     "lbm_batch_set_flow_nodes": ([_H, ctypes.c_int], ctypes.c_int),
+    "lbm_batch_partition": ([ctypes.POINTER(lbm_params), ctypes.c_int, ctypes.c_int,
+                             ctypes.POINTER(ctypes.c_int32), _DP], ctypes.c_int),
     "lbm_batch_get_flow_nodes": ([_H, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "lbm_batch_destroy": ([_H], ctypes.c_int),
 }
@@ -616,6 +618,15 @@ def lbm_batch_autotune(b, reps: int = 3) -> float:
 
 def lbm_batch_set_barrier_test(b, extra_completions: int, spin_limit: int):
     _check(load_library().lbm_batch_set_barrier_test(b, extra_completions, spin_limit))
+
+
+def lbm_batch_partition(params_list, nranks: int):
+    """(owner list, imbalance): the rank of every instance (see the C header)."""
+    arr = (lbm_params * len(params_list))(*params_list)
+    owner = (ctypes.c_int32 * len(params_list))()
+    imb = ctypes.c_double()
+    _check(load_library().lbm_batch_partition(arr, len(params_list), int(nranks), owner, ctypes.byref(imb)))
+    return list(owner), imb.value
 
 
 def lbm_batch_set_flow_nodes(b, nodes: int):
