@@ -383,6 +383,51 @@ int lbm_uses_tile_staging(lbm_handle h, int* width);
  * LBM_EINVAL for spin_limit = 0 or extra_tx_bytes >= 2^20. */
 int lbm_set_stage_test(lbm_handle h, unsigned extra_tx_bytes, unsigned spin_limit);
 
+/* ---- z-slab decomposition (one lattice over several GPUs) ----------------
+ * A lattice of global size nx * ny * NZ split along z over R ranks: each
+ * rank's handle is a lattice of nx * ny * (nz_r + 2) planes, plane 0 and
+ * plane nz_r + 1 being ghost copies of the planes just below and above its
+ * own planes 1 .. nz_r (periodic: rank 0's lower neighbour is rank R - 1).
+ * Initialise each slab with its own planes and the two neighbouring ones
+ * (lbm_init_fields or lbm_set_populations with the global field's planes
+ * z_r - 1 .. z_r + nz_r). The even AA step is local to a node; the odd step
+ * (Eqs. 5, 11 in the in-place pattern) reads the slots opposite to e_z = +-1
+ * from the neighbouring planes and writes slots e_z = +-1 into them, so the
+ * boundary planes reach into the ghost planes at odd steps only. Around every
+ * odd step (lbm_step one step at a time; lbm_step_count even before it) the
+ * ranks exchange two halo buffers each way:
+ *   phase 0, before the step: the e_z = +1 slots of plane 1 go to the lower
+ *     neighbour's upper ghost, the e_z = -1 slots of plane nz_r to the upper
+ *     neighbour's lower ghost;
+ *   phase 1, after the step: the e_z = -1 slots written into the lower ghost
+ *     go back to the lower neighbour's plane nz_r, the e_z = +1 slots written
+ *     into the upper ghost to the upper neighbour's plane 1.
+ * lbm_halo_pack(phase) fills to_lower / to_upper; lbm_halo_unpack(phase)
+ * takes what the lower neighbour sent as its to_upper (from_lower) and what
+ * the upper neighbour sent as its to_lower (from_upper). With one rank the
+ * slab is its own neighbour (from_lower = its to_upper). The exchange itself
+ * (NCCL send/recv, or copies between devices) is the caller's.
+ * In slab mode the step kernels update planes 1 .. nz - 2 only;
+ * lbm_diagnostics reduces the own planes (averages over them: combine ranks
+ * by node count) and returns eps_p and eps_k_curl as NaN (their central
+ * differences would need neighbour fields); lbm_step_diagnostics,
+ * lbm_diagnostics_noalloc, lbm_init_tgv and tile staging are not available. */
+
+/* enable = 1: planes 0 and nz - 1 are ghost planes (nz >= 3, else
+ * LBM_EINVAL); 0: an ordinary periodic lattice. */
+int lbm_set_slab(lbm_handle h, int enable);
+
+/* Bytes of one halo buffer: (number of f slots with e_z = +1 + number of g
+ * slots with e_z = +1) * nx * ny * element size (D3Q27xD3Q19: 9 + 5 planes). */
+int lbm_halo_bytes(lbm_handle h, size_t* bytes);
+
+/* Device buffers (lbm_halo_bytes each, on the handle's device). Enqueued on
+ * the handle's stream (device-to-device copies, one per slot and plane);
+ * return without waiting. LBM_ESTATE without slab mode or store; LBM_EINVAL
+ * for another phase or a null buffer. */
+int lbm_halo_pack(lbm_handle h, int phase, void* to_lower, void* to_upper);
+int lbm_halo_unpack(lbm_handle h, int phase, const void* from_lower, const void* from_upper);
+
 /* Enable (1, default) or disable (0) CUDA-graph replay in lbm_step. */
 int lbm_set_graphs(lbm_handle h, int enable);
 

@@ -90,6 +90,7 @@ struct lbm_ctx {
     int bxo = 0, byo = 0;    // and of the odd ones
     int pairing = LBM_PAIRING_ALL;   // two nodes per thread (16-bit storage, even nx)
     bool tile_staging = false;        // bulk-copy staged kernel where it applies
+    bool slab = false;                // z-slab: planes 0 and nz - 1 are ghost planes (lbm_set_slab)
     int stage_grid = 0;               // persistent grid of the staged kernel (0: not derived yet)
     int* d_err = nullptr;             // device flag raised by a bounded wait that ran out
     uint32_t stage_spin = 1u << 22;   // mbarrier polls per wait
@@ -150,7 +151,7 @@ void derive_phys(lbm_ctx* h)
 // not 16-byte aligned (bulk copies need 16-byte aligned rows).
 int stage_width(const lbm_ctx* h)
 {
-    if (!h->tile_staging || h->ks->staged[h->p.forcing][0] == nullptr || h->store == nullptr) return 0;
+    if (!h->tile_staging || h->slab || h->ks->staged[h->p.forcing][0] == nullptr || h->store == nullptr) return 0;
     if (reinterpret_cast<uintptr_t>(h->store) % 16 != 0) return 0;
     const int nx = h->p.nx;
     return nx % 256 == 0 ? 256 : nx % 128 == 0 ? 128 : nx % 64 == 0 ? 64 : 0;
@@ -299,7 +300,17 @@ DiagArgs diag_args(lbm_ctx* h)
     a.nu = (float)nu;
     a.fields = h->diag_fields;
     a.partials = h->diag_partials;
+    const uint32_t plane = (uint32_t)p.nx * (uint32_t)p.ny;
+    a.idx0 = h->slab ? plane : 0u;
+    a.idx1 = h->slab ? h->geo.n3 - plane : h->geo.n3;
     return a;
+}
+
+// Nodes the diagnostics cover: every node, or a z-slab's own planes.
+double owned_nodes(const lbm_ctx* h)
+{
+    const double plane = (double)h->p.nx * (double)h->p.ny;
+    return h->slab ? (double)h->geo.n3 - 2.0 * plane : (double)h->geo.n3;
 }
 
 // The paper-unit block of a record (Section 2.4: U = L = 1, so one
@@ -323,21 +334,25 @@ void fill_phys(const lbm_params& p, lbm_diag* out)
 int fill_diag(const lbm_ctx* h, int64_t step, lbm_diag* out)
 {
     const double* s = h->diag_host;
-    const double inv = 1.0 / (double)h->geo.n3;
+    const double nodes = owned_nodes(h);
+    const double inv = 1.0 / nodes;
+    const double nan = std::numeric_limits<double>::quiet_NaN();
     out->Ek = s[kDEk] * inv;
     out->Ep = s[kDEp] * inv;
     out->eps_k = s[kDEpsK] * inv;
-    out->eps_p = s[kDEpsP] * inv;
-    out->eps_k_curl = s[kDEpsKCurl] * inv;
-    out->mass_f = (double)h->geo.n3 + s[kDDrho];
-    out->mass_g = (double)h->geo.n3 * h->p.rho0 + s[kDA];
+    // a z-slab has no neighbour fields for the central differences
+    out->eps_p = h->slab ? nan : s[kDEpsP] * inv;
+    out->eps_k_curl = h->slab ? nan : s[kDEpsKCurl] * inv;
+    out->mass_f = nodes + s[kDDrho];
+    out->mass_g = nodes * h->p.rho0 + s[kDA];
     out->mom[0] = s[kDJx];
     out->mom[1] = s[kDJy];
     out->mom[2] = s[kDJz];
     out->umax = s[kDUmax];
     out->step = step;
     fill_phys(h->p, out);
-    for (int q = 0; q < kDNumSlots; ++q)
+    const int checked = h->slab ? kDiagPass1 : kDNumSlots;
+    for (int q = 0; q < checked; ++q)
         if (!std::isfinite(s[q])) return fail(LBM_ENONFINITE, "non-finite diagnostics at step %lld", (long long)step);
     return LBM_OK;
 }
@@ -389,9 +404,14 @@ cudaError_t launch_step(lbm_ctx* h, int odd, cudaStream_t s)
     a.g = g_ptr(h);
     a.geo = h->geo;
     a.ph = h->ph;
+    // a z-slab updates its own planes 1 .. nz - 2; the ghost planes are only
+    // read and written by the boundary planes' odd steps (never wrapped)
+    a.z0 = h->slab ? 1 : 0;
+    dim3 grid = step_grid(h, odd);
+    if (h->slab) grid.z = (unsigned)(h->p.nz - 2);
     void* args[] = {&a};
     const void* k = uses_pairs(h, odd) ? h->ks->step2[h->p.forcing][odd] : h->ks->step[h->p.forcing][odd];
-    return cudaLaunchKernel(k, step_grid(h, odd), step_block(h, odd), args, 0, s);
+    return cudaLaunchKernel(k, grid, step_block(h, odd), args, 0, s);
 }
 
 int flat_grid(const lbm_ctx* h)
@@ -436,6 +456,51 @@ int after_init(lbm_ctx* h)
     h->initialized = true;
     h->step = 0;
     h->odd = 0;
+    return LBM_OK;
+}
+
+// Slots of velocity set q (this library's order) whose e_z equals sign,
+// into slots[] (may be null); returns their number.
+int halo_slots(int q, int sign, int* slots)
+{
+    auto pick = [&](auto lat) {
+        using L = decltype(lat);
+        int n = 0;
+        for (int i = 0; i < L::kQ; ++i)
+            if (L::ez(i) == sign) {
+                if (slots) slots[n] = i;
+                ++n;
+            }
+        return n;
+    };
+    switch (q) {
+    case 7: return pick(Lattice<7>{});
+    case 15: return pick(Lattice<15>{});
+    case 19: return pick(Lattice<19>{});
+    default: return pick(Lattice<27>{});
+    }
+}
+
+// Halo buffer <-> plane z of the store: the f slots with e_z = sign, then the
+// g slots with e_z = sign, nx*ny elements each (one contiguous run per slot
+// and plane in the store). pack = store -> buffer.
+int halo_copy(lbm_ctx* h, int z, int sign, void* buf, bool pack)
+{
+    const size_t es = elem_size(h->p.storage);
+    const size_t plane = (size_t)h->p.nx * (size_t)h->p.ny * es;
+    int slots[27];
+    char* b = static_cast<char*>(buf);
+    for (int part = 0; part < 2; ++part) {
+        const int q = part ? h->q.qg : h->q.qf;
+        char* base = static_cast<char*>(part ? g_ptr(h) : f_ptr(h));
+        const int n = halo_slots(q, sign, slots);
+        for (int k = 0; k < n; ++k) {
+            char* at = base + ((size_t)slots[k] * h->geo.n3) * es + (size_t)z * plane;
+            LBM_CUDA(cudaMemcpyAsync(pack ? b : at, pack ? at : b, plane, cudaMemcpyDeviceToDevice, h->stream),
+                     "halo copy");
+            b += plane;
+        }
+    }
     return LBM_OK;
 }
 
@@ -622,6 +687,8 @@ int lbm_init_tgv(lbm_handle h, uint64_t seed, double noise_amp)
 {
     int rc = check_handle(h);
     if (rc) return rc;
+    if (h->slab) return fail(LBM_EINVAL, "a z-slab is initialised from the global field's planes (lbm_init_fields "
+                                         "or lbm_set_populations), not by lbm_init_tgv");
     if (h->p.nx != h->p.ny || h->p.nx != h->p.nz) return fail(LBM_EINVAL, "the Taylor-Green box needs nx = ny = nz");
     if (!std::isfinite(noise_amp)) return fail(LBM_EINVAL, "non-finite noise amplitude");
     if ((rc = ensure_store(h))) return rc;
@@ -827,12 +894,14 @@ int lbm_diagnostics(lbm_handle h, lbm_diag* out)
     void* args[] = {&a};
     LBM_CUDA(cudaLaunchKernel(h->ks->diag_moments, dim3(h->diag_blocks), dim3(kDiagBlock), args, 0, h->stream),
              "diag pass 1");
-    LBM_CUDA(cudaLaunchKernel(diag_gradients_kernel(), dim3(h->diag_blocks), dim3(kDiagBlock), args, 0, h->stream),
-             "diag pass 2");
+    if (!h->slab)
+        LBM_CUDA(cudaLaunchKernel(diag_gradients_kernel(), dim3(h->diag_blocks), dim3(kDiagBlock), args, 0, h->stream),
+                 "diag pass 2");
     const double* pp = h->diag_partials;
     int nb = h->diag_blocks;
+    int nb2 = h->slab ? 0 : h->diag_blocks;
     double* dout = h->diag_out;
-    void* fargs[] = {&pp, &nb, &nb, &dout};
+    void* fargs[] = {&pp, &nb, &nb2, &dout};
     LBM_CUDA(cudaLaunchKernel(diag_final_kernel(), dim3(1), dim3(kDiagBlock), fargs, 0, h->stream), "diag pass 3");
     LBM_CUDA(cudaMemcpyAsync(h->diag_host, h->diag_out, kDNumSlots * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
              "diag copy");
@@ -847,6 +916,7 @@ int lbm_step_diagnostics(lbm_handle h, int64_t nsteps, lbm_diag* out)
     if (!out) return fail(LBM_EINVAL, "null output");
     if (nsteps < 1) return fail(LBM_EINVAL, "lbm_step_diagnostics needs at least one step");
     if (!h->initialized) return fail(LBM_ESTATE, "lbm_step_diagnostics before initialisation");
+    if (h->slab) return fail(LBM_EUNSUPPORTED, "a z-slab steps with lbm_step and reports with lbm_diagnostics");
     const int odd = h->odd;
     const bool pairs = uses_pairs(h, odd);
     const dim3 grid = step_grid(h, odd);
@@ -1172,6 +1242,54 @@ int lbm_set_stage_test(lbm_handle h, unsigned extra_tx_bytes, unsigned spin_limi
     return LBM_OK;
 }
 
+int lbm_set_slab(lbm_handle h, int enable)
+{
+    if (!h) return fail(LBM_EINVAL, "null handle");
+    if (enable && h->p.nz < 3) return fail(LBM_EINVAL, "a z-slab needs nz >= 3 (two ghost planes and one of its own)");
+    h->slab = enable != 0;
+    h->stage_grid = 0;
+    drop_graph(h);
+    return LBM_OK;
+}
+
+int lbm_halo_bytes(lbm_handle h, size_t* bytes)
+{
+    if (!h || !bytes) return fail(LBM_EINVAL, "null argument");
+    *bytes = (size_t)(halo_slots(h->q.qf, 1, nullptr) + halo_slots(h->q.qg, 1, nullptr)) * (size_t)h->p.nx *
+             (size_t)h->p.ny * elem_size(h->p.storage);
+    return LBM_OK;
+}
+
+int lbm_halo_pack(lbm_handle h, int phase, void* to_lower, void* to_upper)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!h->slab) return fail(LBM_ESTATE, "halo exchange without lbm_set_slab");
+    if (!h->store) return fail(LBM_ESTATE, "halo exchange before the store exists");
+    if (phase != 0 && phase != 1) return fail(LBM_EINVAL, "phase must be 0 (before an odd step) or 1 (after it)");
+    if (!to_lower || !to_upper) return fail(LBM_EINVAL, "null buffer");
+    const int top = h->p.nz - 1;
+    // phase 0: own boundary planes (plane 1: e_z = +1 slots; plane nz-2: e_z = -1)
+    // phase 1: ghost planes (plane 0: e_z = -1 slots; plane nz-1: e_z = +1)
+    if ((rc = halo_copy(h, phase ? 0 : 1, phase ? -1 : +1, to_lower, true))) return rc;
+    return halo_copy(h, phase ? top : top - 1, phase ? +1 : -1, to_upper, true);
+}
+
+int lbm_halo_unpack(lbm_handle h, int phase, const void* from_lower, const void* from_upper)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!h->slab) return fail(LBM_ESTATE, "halo exchange without lbm_set_slab");
+    if (!h->store) return fail(LBM_ESTATE, "halo exchange before the store exists");
+    if (phase != 0 && phase != 1) return fail(LBM_EINVAL, "phase must be 0 (before an odd step) or 1 (after it)");
+    if (!from_lower || !from_upper) return fail(LBM_EINVAL, "null buffer");
+    const int top = h->p.nz - 1;
+    // phase 0: into the ghost planes (plane 0: e_z = -1 slots; plane nz-1: e_z = +1)
+    // phase 1: into the own boundary planes (plane 1: e_z = +1; plane nz-2: e_z = -1)
+    if ((rc = halo_copy(h, phase ? 1 : 0, phase ? +1 : -1, const_cast<void*>(from_lower), false))) return rc;
+    return halo_copy(h, phase ? top - 1 : top, phase ? -1 : +1, const_cast<void*>(from_upper), false);
+}
+
 int lbm_set_graphs(lbm_handle h, int enable)
 {
     if (!h) return fail(LBM_EINVAL, "null handle");
@@ -1243,6 +1361,7 @@ int lbm_diagnostics_noalloc(lbm_handle h, lbm_diag* out)
                     "use lbm_diagnostics",
                     n3, (unsigned)kStaticMaxBlocks * kStaticNodesPerBlock);
     if (!h->initialized) return fail(LBM_ESTATE, "diagnostics before initialisation");
+    if (h->slab) return fail(LBM_EUNSUPPORTED, "allocation-free diagnostics of a z-slab (use lbm_diagnostics)");
     double* scratch = nullptr;
     if ((rc = static_scratch_address(h->device, &scratch))) return rc;
     // the moment pass strides over the lattice, so the grid fills the GPU
@@ -1268,6 +1387,8 @@ int lbm_diagnostics_noalloc(lbm_handle h, lbm_diag* out)
     a.nu = (float)nu;
     a.fields = nullptr;      // no field scratch: the central-difference pass is skipped
     a.partials = scratch;    // every block overwrites its own record, nothing needs clearing
+    a.idx0 = 0;
+    a.idx1 = n3;
     void* args[] = {&a};
     LBM_CUDA(cudaLaunchKernel(h->ks->diag_moments, dim3(blocks), dim3(kDiagBlock), args, 0, h->stream),
              "static diag pass 1");

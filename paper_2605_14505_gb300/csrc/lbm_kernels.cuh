@@ -31,6 +31,7 @@ struct DiagArgs {
     float nu;
     float* fields;       // 4 * n3: rho', ux, uy, uz (written by pass 1, read by pass 2)
     double* partials;    // gridDim.x * kDNumSlots
+    uint32_t idx0, idx1; // pass 1 reduces nodes [idx0, idx1) (a z-slab: its own planes only)
 };
 
 // Compensated (Kahan) FP32 running sum for a thread's share of a diagnostics
@@ -229,6 +230,7 @@ struct StepArgs {
     Geometry geo;
     Phys ph;
     DiagSink dg;      // used by the diagnosing variants only
+    int z0;           // first z-plane of the launch (1 for a z-slab with ghost planes, else 0)
 };
 
 // The fused AA update of one node: load the QF + QG populations (coalesced
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(256, kStepMinBlocks<P>) k_step(StepArgs args)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
+    const int z = blockIdx.z + args.z0;
     if (x >= args.geo.nx || y >= args.geo.ny) return;
     update_node<P, FORCING, T, ODD>(args.f, args.g, args.geo, args.ph, x, y, z);
 }
@@ -614,7 +616,7 @@ __global__ void __launch_bounds__(256, kStep2MinBlocks<P>) k_step2(StepArgs args
 {
     const int x0 = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
+    const int z = blockIdx.z + args.z0;
     if (x0 >= args.geo.nx || y >= args.geo.ny) return;
     update_pair<P, FORCING, T, ODD>(args, x0, y, z, NoHook{});
 }
@@ -958,7 +960,8 @@ __global__ void __launch_bounds__(kDiagBlock) k_diag_moments(DiagArgs a)
     const uint32_t n3 = a.geo.n3;
     const DiagSink sink{a.ep_scale, a.epsk_scale, a.s_scale, a.fields, a.partials};
     DiagAcc d;
-    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n3; idx += gridDim.x * blockDim.x) {
+    for (uint32_t idx = a.idx0 + blockIdx.x * blockDim.x + threadIdx.x; idx < a.idx1;
+         idx += gridDim.x * blockDim.x) {
         int x, y, z;
         node_xyz(a.geo, idx, x, y, z);
         const NodeAddr na = node_addr<T>(a.geo, x, y, z);

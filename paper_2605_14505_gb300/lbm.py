@@ -133,6 +133,10 @@ _SIGS = {
     "lbm_get_block": ([_H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "lbm_autotune": ([_H, ctypes.c_int, _DP], ctypes.c_int),
     "lbm_set_graphs": ([_H, ctypes.c_int], ctypes.c_int),
+    "lbm_set_slab": ([_H, ctypes.c_int], ctypes.c_int),
+    "lbm_halo_bytes": ([_H, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "lbm_halo_pack": ([_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "lbm_halo_unpack": ([_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "lbm_set_pairing": ([_H, ctypes.c_int], ctypes.c_int),
     "lbm_set_tile_staging": ([_H, ctypes.c_int], ctypes.c_int),
     "lbm_uses_tile_staging": ([_H, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -446,6 +450,24 @@ def lbm_uses_tile_staging(h) -> int:
 
 def lbm_set_stage_test(h, extra_tx_bytes: int, spin_limit: int):
     _check(load_library().lbm_set_stage_test(h, int(extra_tx_bytes), int(spin_limit)))
+
+
+def lbm_set_slab(h, enable: bool):
+    _check(load_library().lbm_set_slab(h, 1 if enable else 0))
+
+
+def lbm_halo_bytes(h) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().lbm_halo_bytes(h, ctypes.byref(n)))
+    return n.value
+
+
+def lbm_halo_pack(h, phase: int, to_lower: int, to_upper: int):
+    _check(load_library().lbm_halo_pack(h, int(phase), ctypes.c_void_p(to_lower), ctypes.c_void_p(to_upper)))
+
+
+def lbm_halo_unpack(h, phase: int, from_lower: int, from_upper: int):
+    _check(load_library().lbm_halo_unpack(h, int(phase), ctypes.c_void_p(from_lower), ctypes.c_void_p(from_upper)))
 
 
 def lbm_set_graphs(h, enable: bool):
