@@ -532,6 +532,21 @@ def run_ncu_case(args):
 
     from paper_2605_14505_gb300 import lbm
 
+    if args.ncu_case == "batch-inst":
+        # the 64-instance sweep under the per-instance driver (each instance's
+        # own step kernel and default launch shapes, no autotuning): init,
+        # then ncu_steps steps, for a bounded launch list with DRAM bytes
+        specs = sweep_specs()
+        params = [lbm.lbm_params_from_physics(n, n, n, pair, f, Re, Fr, 1.0, U0) for n, pair, f, Re, Fr in specs]
+        b = lbm.lbm_batch_create(params)
+        lbm.lbm_batch_set_mode(b, "instances")
+        lbm.lbm_batch_init_tgv(b, seed=1, noise_amp=1e-3)
+        lbm.lbm_batch_step(b, args.ncu_steps)
+        lbm.lbm_batch_synchronize(b)
+        lbm.lbm_batch_destroy(b)
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": args.ncu_case, "steps": args.ncu_steps, "sources": source_fingerprint()}))
+        return
     if args.ncu_case in ("batch", "batch-step"):
         # the 64-instance sweep: persistent driver, `ncu_steps` steps per launch;
         # or the per-step driver (one launch per variant and step, below the
@@ -576,15 +591,22 @@ X1_U0 = 0.05 / 3 ** 0.5   # Ma 0.05 (Section 3.1)
 
 
 def paper_series(n, pair, forcing, Re, Fr, Sc, U0, t_end, storage="fp32", seed=1, noise_amp=0.0,
-                 spectrum_at=None, every_tc=0.1):
+                 spectrum_at=None, every_tc=0.1, pressure=False):
     """Diagnostics every ~every_tc convective times to t_end (lbm_step_diagnostics:
     reduced inside the step kernel), and optionally the kinetic-energy spectrum of
-    the first sample at t >= spectrum_at (fields written to device memory, cuFFT)."""
+    the first sample at t >= spectrum_at (fields written to device memory, cuFFT).
+    pressure: start from rho = 1 + p / cs^2 with the Taylor-Green pressure
+    instead of rho = 1 (fewer sound waves at the start)."""
+    import stgv_inputs as inputs
     from paper_2605_14505_gb300 import lbm, post
 
     p = lbm.lbm_params_from_physics(n, n, n, pair, forcing, Re, Fr, Sc, U0)
     sim = lbm.Simulation(p, storage=storage)
-    sim.init_tgv(seed=seed, noise_amp=noise_amp)
+    if pressure:
+        _, u, rp = inputs.tgv_fields(n, U0, seed=seed, noise_amp=noise_amp)
+        sim.init_fields(post.tgv_pressure_density(n, U0), u, rp)
+    else:
+        sim.init_tgv(seed=seed, noise_amp=noise_amp)
     steps_tc = p.L / U0
     every = max(1, round(every_tc * steps_tc))
     total = round(t_end * steps_tc)
@@ -623,17 +645,21 @@ def run_validation(args):
     from paper_2605_14505_gb300 import lbm, post
 
     out = {"mode": "validation", "lattice": 256}
+    dump = {}
     todo = set(args.validation.split(",")) if args.validation != "all" else {"x1", "froude", "storage"}
     if "x1" in todo:
         x1 = {}
         for Re in X1_RE:
-            ser, _, secs = paper_series(256, "27x19", "guo", Re, float("inf"), 1.0, X1_U0, args.x1_tend)
+            ser, _, secs = paper_series(256, "27x19", "guo", Re, float("inf"), 1.0, X1_U0, args.x1_tend,
+                                        pressure=True)
             ph = post.to_physical(ser)
+            dump[f"x1_Re{int(Re)}"] = {k: v.tolist() for k, v in ph.items()}
             rate = post.total_dissipation_rate(ph["t"], ph["Ek"])
             m = (ph["t"] >= 0.5) & (ph["t"] <= 3.0)
             pk = post.peaks(ph["t"], rate, 1)
             x1[str(int(Re))] = {
-                "laminar_max_rel_diff": float(np.max(np.abs(rate[m] / ph["eps_k"][m] - 1))),
+                "laminar_window_balance": post.energy_balance(ph["t"], ph["Ek"], ph["eps_k"], 0.5, 3.0),
+                "laminar_max_pointwise_rel_diff": float(np.max(np.abs(rate[m] / ph["eps_k"][m] - 1))),
                 "peak_t": pk[0][0] if pk else None, "peak_eps": pk[0][1] if pk else None,
                 "finite": bool(np.all(np.isfinite(ph["Ek"]))), "samples": len(ser), "secs": round(secs, 1)}
             print("x1", Re, x1[str(int(Re))], file=sys.stderr, flush=True)
@@ -646,12 +672,15 @@ def run_validation(args):
             if Fr == 1.0:
                 ref_series = ser
             ph = post.to_physical(ser)
+            dump[f"froude_{Fr}"] = {k: v.tolist() for k, v in ph.items()}
             t = ph["t"]
             rate = post.total_dissipation_rate(t, ph["Etot"])
             R = post.buoyancy_reynolds(ph["eps_k"], PAPER["Re"], Fr)
             gam = post.flux_coefficient(ph["eps_p"], ph["eps_k"])
-            rec = {"dissipation_peaks": post.peaks(t, rate, 2), "eps_sum_peaks": post.peaks(t, ph["eps_k"] + ph["eps_p"], 2),
-                   "R_peaks": post.peaks(t, R, 2), "Gamma_max": [float(t[np.argmax(gam[1:]) + 1]), float(np.max(gam[1:]))],
+            rec = {"dissipation_peaks": post.peaks(t, rate, 2, separation=2.0),
+                   "eps_sum_peaks": post.peaks(t, ph["eps_k"] + ph["eps_p"], 2, separation=2.0),
+                   "R_peaks": post.peaks(t, R, 2, separation=2.0),
+                   "Gamma_max": [float(t[np.argmax(gam[1:]) + 1]), float(np.max(gam[1:]))],
                    "Gamma_b": float(post.bulk_flux_coefficient(t, ph["eps_p"], ph["eps_k"])),
                    "Fr_t": float(post.turbulent_froude(t, ph["eps_k"], ph["Ek"], Fr)),
                    "Ek_end": float(ph["Ek"][-1]), "Ep_max": float(np.max(ph["Ep"])),
@@ -676,6 +705,9 @@ def run_validation(args):
                 st[storage]["secs"] = round(secs, 1)
             out["storage_rule_fr1"] = st
             print("storage", st, file=sys.stderr, flush=True)
+    if args.validation_out:
+        with open(args.validation_out, "w") as fh:
+            json.dump(dump, fh)
     print(json.dumps(out))
 
 
@@ -694,7 +726,8 @@ def main():
                     help="steps of the 256^3 workload series for the storage rule (0: skip it)")
     ap.add_argument("--sweep-steps", type=int, default=SWEEP_STEPS,
                     help="timed steps of the batched sweep (fewer for a bounded profiler launch list)")
-    ap.add_argument("--ncu-case", choices=["fp32", "fp16", "bf16", "19x7", "19x7-fp16", "batch", "batch-step"],
+    ap.add_argument("--ncu-case", choices=["fp32", "fp16", "bf16", "19x7", "19x7-fp16", "batch", "batch-step",
+                                           "batch-inst"],
                     default=None,
                     help="run a small profiling case instead of the benchmark")
     ap.add_argument("--ncu-n", type=int, default=128)
@@ -707,6 +740,7 @@ def main():
                     help="run the paper's validation runs instead of the benchmark: all, or a comma list of "
                          "x1, froude, storage")
     ap.add_argument("--x1-tend", type=float, default=14.0, help="end time of the unstratified runs")
+    ap.add_argument("--validation-out", default=None, help="file for the validation runs' series (paper units)")
     args = ap.parse_args()
     if args.validation:
         run_validation(args)

@@ -117,11 +117,39 @@ def spectral_slope(k, E, kmin: float, kmax: float) -> float:
     return float(np.polyfit(np.log(k[m]), np.log(E[m]), 1)[0])
 
 
-def peaks(t, y, count: int = 2):
-    """The `count` highest interior local maxima of a sampled series, as
-    (t, y) pairs in time order."""
+def peaks(t, y, count: int = 2, separation: float = 0.0):
+    """The `count` highest interior local maxima of a sampled series at least
+    `separation` apart in t (highest first, then the next highest outside the
+    chosen ones' windows), as (t, y) pairs in time order."""
     t = np.asarray(t, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
     idx = [i for i in range(1, len(y) - 1) if y[i] > y[i - 1] and y[i] >= y[i + 1]]
-    idx = sorted(sorted(idx, key=lambda i: -y[i])[:count])
-    return [(float(t[i]), float(y[i])) for i in idx]
+    chosen = []
+    for i in sorted(idx, key=lambda i: -y[i]):
+        if all(abs(t[i] - t[j]) >= separation for j in chosen):
+            chosen.append(i)
+        if len(chosen) == count:
+            break
+    return [(float(t[i]), float(y[i])) for i in sorted(chosen)]
+
+
+def energy_balance(t, Ek, eps, t0: float, t1: float) -> float:
+    """Relative mismatch of the kinetic-energy budget over [t0, t1]:
+    (E_k(t0) - E_k(t1)) / int_t0^t1 eps dt - 1, i.e. the window average of
+    -dE_k/dt against that of eps (trapezoidal rule on the samples)."""
+    t = np.asarray(t, dtype=np.float64)
+    m = (t >= t0 - 1e-12) & (t <= t1 + 1e-12)
+    tw, ew = t[m], np.asarray(eps, dtype=np.float64)[m]
+    kw = np.asarray(Ek, dtype=np.float64)[m]
+    return float((kw[0] - kw[-1]) / _trapezoid(ew, tw) - 1.0)
+
+
+def tgv_pressure_density(n: int, U0: float, cs2: float = 1.0 / 3.0):
+    """rho = 1 + p / cs^2 with the Taylor-Green pressure
+    p = (U0^2 / 16) (cos 2x + cos 2y) (cos 2z + 2) on the vertex grid (the
+    standard form of the initial pressure that Eq. 21 prints garbled), in
+    lattice units, flat x fastest."""
+    x = np.arange(n) * (2.0 * np.pi / n)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    p = (U0 ** 2 / 16.0) * (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0)
+    return (1.0 + p / cs2).ravel()

@@ -58,3 +58,17 @@ def test_spectral_slope_and_peaks():
     y = np.exp(-((t - 11.5) / 1.0) ** 2) + 0.8 * np.exp(-((t - 16.5) / 1.0) ** 2) + 0.3 * np.exp(-((t - 3) / 0.5) ** 2)
     p = post.peaks(t, y, 2)
     assert [round(a, 2) for a, _ in p] == [11.5, 16.5]
+    # a wiggle on the main peak is not a second peak when a separation is asked for
+    y2 = y + 0.02 * np.sin(40 * t) * np.exp(-((t - 11.5) / 1.0) ** 2)
+    p2 = post.peaks(t, y2, 2, separation=2.0)
+    assert abs(p2[0][0] - 11.5) < 0.3 and abs(p2[1][0] - 16.5) < 0.3
+
+
+def test_energy_balance_and_pressure_field():
+    t = np.linspace(0, 4, 81)
+    eps = 0.01 * np.exp(-0.3 * t)
+    Ek = 0.125 - 0.01 / 0.3 * (1 - np.exp(-0.3 * t))   # dE/dt = -eps exactly
+    assert abs(post.energy_balance(t, Ek, eps, 0.5, 3.0)) < 1e-4
+    rho = post.tgv_pressure_density(8, 0.04)
+    # mean of (cos 2x + cos 2y)(cos 2z + 2) over the grid is 0: mass unchanged
+    assert abs(rho.mean() - 1.0) < 1e-15 and rho.max() > 1.0
