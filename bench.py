@@ -383,7 +383,7 @@ def storage_rule_series(args) -> dict:
         return d
 
     res = {"fp16": {}, "bf16": {}}
-    for name in G.SERIES:
+    for name in ("stgv64_re200_fr01_sc", "stgv64_paper_re1600_fr1_sc"):
         n, (qf, qg), forcing, Re, Fr, Sc, U0_, steps, every, seed, amp = G.SERIES[name]
         ref = G.read(name)
         for storage in res:

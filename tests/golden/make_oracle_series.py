@@ -34,6 +34,12 @@ SERIES = {
     # turbulent breakdown and its dissipation peaks (Section 3.3)
     "stgv64_paper_re1600_fr1_sc": (64, (27, 19), "sc", 1600.0, 1.0, 0.7, 0.0577, 5310, 18, 1, 1e-3),
 }
+# the 128^3 workload: both stencil pairs x {Guo, Shan-Chen} x Fr {0.5, 0.1}, Re 400,
+# 5000 steps with the diagnostics every 50 steps
+for _q in ((19, 7), (27, 19)):
+    for _f in ("guo", "sc"):
+        for _fr in (0.5, 0.1):
+            SERIES[f"c1_128_q{_q[0]}q{_q[1]}_{_f}_fr{_fr}"] = (128, _q, _f, 400.0, _fr, 1.0, 0.04, 5000, 50, 1, 1e-3)
 
 COLUMNS = ("step", "Ek", "Ep", "eps_k", "eps_p", "eps_k_curl", "mass_f", "mass_g", "mom_x", "mom_y",
            "mom_z", "umax")
