@@ -43,7 +43,7 @@ WORKLOAD = "stratified TGV 256^3, D3Q27xD3Q19, velocity-shift (Shan-Chen) forcin
 # (dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture, mean of
 # an even and an odd launch), with the fingerprint of the kernel sources the
 # capture ran; reported as null once the sources differ from it.
-NCU_TRAFFIC = {"fingerprint": "1908a1c5fa322710", "fp32": 6115913088, "fp16": 3027408000, "bf16": 3027413504}
+NCU_TRAFFIC = {"fingerprint": "7d72ec5d9668c8bc", "fp32": 6115758976, "fp16": 3028256128, "bf16": 3028244224}
 
 
 def source_fingerprint() -> str:
@@ -541,8 +541,18 @@ def run_ncu_case(args):
         b = lbm.lbm_batch_create(params)
         lbm.lbm_batch_set_mode(b, "instances")
         lbm.lbm_batch_init_tgv(b, seed=1, noise_amp=1e-3)
+        if args.ncu_range:
+            # warm the caches and graphs, then bracket the measured steps with
+            # cudaProfilerStart/Stop (an ncu range, all streams together)
+            lbm.lbm_batch_step(b, args.ncu_steps)
+            lbm.lbm_batch_synchronize(b)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
         lbm.lbm_batch_step(b, args.ncu_steps)
         lbm.lbm_batch_synchronize(b)
+        if args.ncu_range:
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
         lbm.lbm_batch_destroy(b)
         torch.cuda.synchronize()
         print(json.dumps({"ncu_case": args.ncu_case, "steps": args.ncu_steps, "sources": source_fingerprint()}))
@@ -731,6 +741,8 @@ def main():
                     default=None,
                     help="run a small profiling case instead of the benchmark")
     ap.add_argument("--ncu-n", type=int, default=128)
+    ap.add_argument("--ncu-range", action="store_true",
+                    help="profiling case batch-inst: measured steps inside cudaProfilerStart/Stop")
     ap.add_argument("--ncu-steps", type=int, default=6)
     ap.add_argument("--ncu-pairing", choices=["off", "all", "even"], default="all",
                     help="profiling case: nodes per thread for 16-bit storage (lbm_set_pairing)")
