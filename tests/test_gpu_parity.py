@@ -184,8 +184,8 @@ def test_c0_diagnostics_series():
 @pytest.mark.parametrize("storage,tol", [("fp16", 0.01), ("bf16", 0.05)])
 def test_reduced_precision_storage_error(storage, tol):
     """FP16/BF16 deviation storage with FP32 arithmetic: E_k, E_p, eps_k within
-    `tol` of the FP64 oracle over 1000 steps of the 32^3 SC case (north-star
-    budget 1% for FP16; BF16 keeps 8 mantissa bits and is reported at 5%)."""
+    `tol` of the FP64 oracle over 1000 steps of the 32^3 SC case (the precision
+    target's 1 % for FP16; BF16 keeps 8 mantissa bits and is reported at 5 %)."""
     p, g, o, series = _run_both(32, "27x19", "sc", 100.0, 0.5, 1000, storage=storage, every=100)
     ep_max = max(s[1]["Ep"] for s in series)
     for dg, do in series:
