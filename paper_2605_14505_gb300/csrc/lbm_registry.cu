@@ -17,6 +17,11 @@ const KernelSet* kernels_q19q19_f32();
 const KernelSet* kernels_q19q15_f32();
 const KernelSet* kernels_q15q7_f32();
 const KernelSet* kernels_q7q27_f32();
+const KernelSet* kernels_q27q27_f16();
+const KernelSet* kernels_q19q19_f16();
+const KernelSet* kernels_q19q15_f16();
+const KernelSet* kernels_q15q7_f16();
+const KernelSet* kernels_q7q27_f16();
 
 const KernelSet* kernel_set(int pair, int storage)
 {
@@ -24,12 +29,13 @@ const KernelSet* kernel_set(int pair, int storage)
     switch (pair) {
     case 0: return storage == 0 ? kernels_q27q19_f32() : storage == 1 ? kernels_q27q19_f16() : kernels_q27q19_bf16();
     case 1: return storage == 0 ? kernels_q19q7_f32() : storage == 1 ? kernels_q19q7_f16() : kernels_q19q7_bf16();
-    // the paper's other pairs (Sections 3.2-3.3), FP32 storage
-    case 2: return storage == 0 ? kernels_q27q27_f32() : nullptr;
-    case 3: return storage == 0 ? kernels_q19q19_f32() : nullptr;
-    case 4: return storage == 0 ? kernels_q19q15_f32() : nullptr;
-    case 5: return storage == 0 ? kernels_q15q7_f32() : nullptr;
-    case 6: return storage == 0 ? kernels_q7q27_f32() : nullptr;
+    // the paper's other pairs (Sections 3.2-3.3), FP32 and FP16 storage (the
+    // 16-bit storage rule keeps FP16; BF16 misses it on the headline pair)
+    case 2: return storage == 0 ? kernels_q27q27_f32() : storage == 1 ? kernels_q27q27_f16() : nullptr;
+    case 3: return storage == 0 ? kernels_q19q19_f32() : storage == 1 ? kernels_q19q19_f16() : nullptr;
+    case 4: return storage == 0 ? kernels_q19q15_f32() : storage == 1 ? kernels_q19q15_f16() : nullptr;
+    case 5: return storage == 0 ? kernels_q15q7_f32() : storage == 1 ? kernels_q15q7_f16() : nullptr;
+    case 6: return storage == 0 ? kernels_q7q27_f32() : storage == 1 ? kernels_q7q27_f16() : nullptr;
     default: return nullptr;
     }
 }

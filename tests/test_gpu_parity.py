@@ -368,6 +368,36 @@ def test_other_stencil_pairs(pair, forcing):
         assert abs(dg[key] - do[key]) <= 2e-5 * abs(do[key]) + 1e-14, (key, dg[key], do[key])
 
 
+@pytest.mark.parametrize("pair", ["27x27", "19x19", "19x15", "15x7", "7x27"])
+@pytest.mark.parametrize("forcing", ["guo", "sc"])
+def test_other_stencil_pairs_fp16(pair, forcing):
+    """The paper's other stencil pairs with FP16 deviation storage (pair
+    kernel, even nx): one and two steps against the oracle started from the
+    same FP16-representable populations, within the storage rounding."""
+    N = 3e-3
+    nx, ny, nz = 36, 10, 6
+    p = lattice_params(nx, ny, nz, pair, forcing, 0.56, 0.58, N * LAM, -N / LAM)
+    qf, qg = lbm.PAIR_Q[p.pair]
+    g = gpu_sim(p, "fp16")
+    n3 = nx * ny * nz
+    rho, u, rp = I.random_fields(nx, ny, nz, 17, 0.05, 0.01, 0.02 / LAM)
+    g.init_fields(rho, u, rp, I.neq_noise(n3, 18), I.neq_noise(n3, 19), 1e-3)
+    o = oracle_for(p)
+    f0, g0 = g.populations()
+    o.set_populations(f0[np.argsort(slot_map(qf))], g0[np.argsort(slot_map(qg))])
+    _, wf, _ = lbm.lbm_velocity_set(qf)
+    _, wg, _ = lbm.lbm_velocity_set(qg)
+    for _ in range(2):
+        g.step(1)
+        o.step(1)
+        fg, gg = g.populations()
+        fo, go = o.populations()
+        fo, go = fo[slot_map(qf)], go[slot_map(qg)]
+        df, dg = fo - wf[:, None], go - p.rho0 * wg[:, None]
+        assert np.max(np.abs(fg - fo)) <= 2.0 ** -10 * np.max(np.abs(df)) + 2.0 ** -23, pair
+        assert np.max(np.abs(gg - go)) <= 2.0 ** -10 * np.max(np.abs(dg)) + 2.0 ** -23, pair
+
+
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
 @pytest.mark.parametrize("shape", [(1, 1, 1), (33, 5, 3), (7, 2, 9)])
 def test_16bit_odd_nx_one_node_kernel_against_oracle(storage, shape):
