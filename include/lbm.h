@@ -407,6 +407,11 @@ int lbm_set_stage_test(lbm_handle h, unsigned extra_tx_bytes, unsigned spin_limi
  * the upper neighbour sent as its to_lower (from_upper). With one rank the
  * slab is its own neighbour (from_lower = its to_upper). The exchange itself
  * (NCCL send/recv, or copies between devices) is the caller's.
+ * After an odd step count the store keeps a node's populations at neighbour
+ * locations (the AA layout), so reading a slab then (lbm_diagnostics,
+ * lbm_get_fields, lbm_get_populations) needs the neighbours' current slots in
+ * the ghost planes: a phase-0 exchange first (harmless to repeat before the
+ * next odd step). After an even step count every read is local.
  * In slab mode the step kernels update planes 1 .. nz - 2 only;
  * lbm_diagnostics reduces the own planes (averages over them: combine ranks
  * by node count) and returns eps_p and eps_k_curl as NaN (their central

@@ -1916,8 +1916,12 @@ int lbm_batch_step(lbm_batch b, int64_t nsteps)
     }
     while (nsteps > 0) {
         if (b->mode == LBM_BATCH_PERSISTENT) {
-            const int k = (int)(nsteps < b->chunk ? nsteps : b->chunk);
-            if (b->stream != nullptr && k == b->chunk)
+            // queue positions are 32-bit: steps * tiles per step (plus the
+            // grid's claims past the end) must stay below 2^32
+            const int64_t kmax = (int64_t)((0xffffffffull - 2ull * (uint64_t)b->persistent_grid) / b->flow_tiles);
+            const int64_t chunk = std::min<int64_t>(b->chunk, std::max<int64_t>(kmax, 1));
+            const int k = (int)(nsteps < chunk ? nsteps : chunk);
+            if (b->stream != nullptr && k == chunk)
                 LBM_CUDA(batch_persistent_graph(b, k, b->odd), "persistent batch graph");
             else
                 LBM_CUDA(batch_launch_persistent(b, k, b->odd, b->stream), "persistent batch launch");
