@@ -82,7 +82,8 @@ def test_x1_laminar_energy_budget_at_256cubed(Re):
     _, u, rp = I.tgv_fields(n, U0)
     sim.init_fields(post.tgv_pressure_density(n, U0), u, rp)
     every = round(0.1 * p.L / U0)
-    series = [sim.step_diagnostics(every) for _ in range(round(3.0 * p.L / U0 / every) + 1)]
+    # each record is the state before its interval: the last one at or past t = 3
+    series = [sim.step_diagnostics(every) for _ in range(int(np.ceil(3.0 * p.L / U0 / every)) + 1)]
     sim.close()
     ph = post.to_physical(series)
     assert ph["t"][-1] >= 3.0
