@@ -675,7 +675,8 @@ def run_validation(args):
 
     out = {"mode": "validation", "lattice": 256}
     dump = {}
-    todo = set(args.validation.split(",")) if args.validation != "all" else {"x1", "froude", "storage"}
+    todo = set(args.validation.split(",")) if args.validation != "all" else \
+        {"x1", "froude", "storage", "stencils", "resolution"}
     if "x1" in todo:
         x1 = {}
         for Re in X1_RE:
@@ -734,6 +735,39 @@ def run_validation(args):
                 st[storage]["secs"] = round(secs, 1)
             out["storage_rule_fr1"] = st
             print("storage", st, file=sys.stderr, flush=True)
+    if "stencils" in todo or "resolution" in todo:
+        # Sections 3.2-3.3: every stencil pair at 256^3, and D3Q27xD3Q19 at 64^3 and
+        # 128^3, at the paper's parameters (Fr0 = 1) to t = 30; peak heights
+        # relative to the D3Q27xD3Q19 256^3 run
+        runs = []
+        if "stencils" in todo:
+            runs += [(256, pair) for pair in ("27x19", "27x27", "19x19", "19x15", "15x7", "7x27", "19x7")]
+        if "resolution" in todo:
+            runs += [(64, "27x19"), (128, "27x19")] + ([] if "stencils" in todo else [(256, "27x19")])
+        res, ref = {}, None
+        for n, pair in runs:
+            ser, _, secs = paper_series(n, pair, PAPER["forcing"], PAPER["Re"], 1.0, PAPER["Sc"], PAPER["U0"], 30.0)
+            ph = post.to_physical(ser)
+            dump[f"pair_{pair}_n{n}"] = {k: v.tolist() for k, v in ph.items()}
+            t = ph["t"]
+            rate = post.total_dissipation_rate(t, ph["Etot"])
+            eps = ph["eps_k"] + ph["eps_p"]
+            rec = {"dissipation_peaks": post.peaks(t, rate, 2, separation=2.0),
+                   "eps_sum_peaks": post.peaks(t, eps, 2, separation=2.0),
+                   "R_peaks": post.peaks(t, post.buoyancy_reynolds(ph["eps_k"], PAPER["Re"], 1.0), 2, separation=2.0),
+                   "Ek_t30": float(ph["Ek"][-1]), "Ep_t30": float(ph["Ep"][-1]), "Ep_max": float(np.max(ph["Ep"])),
+                   "finite": bool(np.all(np.isfinite(ph["Ek"]))), "samples": len(ser), "secs": round(secs, 1)}
+            if n == 256 and pair == "27x19":
+                ref = rec
+            res[f"{pair}@{n}"] = rec
+            print("pairs/resolution", pair, n, rec, file=sys.stderr, flush=True)
+        if ref is not None:
+            rp = [v for _, v in ref["eps_sum_peaks"]]
+            for key, rec in res.items():
+                hp = [v for _, v in rec["eps_sum_peaks"]]
+                if len(hp) == len(rp) == 2:
+                    rec["eps_sum_peaks_rel_to_27x19_256"] = [hp[0] / rp[0], hp[1] / rp[1]]
+        out["stencils_resolution"] = res
     if args.validation_out:
         with open(args.validation_out, "w") as fh:
             json.dump(dump, fh)
@@ -769,7 +803,7 @@ def main():
                     help="profiling case: bulk-copy tile staging for 16-bit storage (lbm_set_tile_staging)")
     ap.add_argument("--validation", default=None,
                     help="run the paper's validation runs instead of the benchmark: all, or a comma list of "
-                         "x1, froude, storage")
+                         "x1, froude, storage, stencils, resolution")
     ap.add_argument("--x1-tend", type=float, default=14.0, help="end time of the unstratified runs")
     ap.add_argument("--validation-out", default=None, help="file for the validation runs' series (paper units)")
     args = ap.parse_args()
