@@ -429,7 +429,8 @@ int lbm_halo_bytes(lbm_handle h, size_t* bytes);
 /* Device buffers (lbm_halo_bytes each, on the handle's device). Enqueued on
  * the handle's stream (device-to-device copies, one per slot and plane);
  * return without waiting. LBM_ESTATE without slab mode or store; LBM_EINVAL
- * for another phase or a null buffer. */
+ * for another phase, or a buffer that is null or not device memory of the
+ * handle's device. */
 int lbm_halo_pack(lbm_handle h, int phase, void* to_lower, void* to_upper);
 int lbm_halo_unpack(lbm_handle h, int phase, const void* from_lower, const void* from_upper);
 

@@ -481,6 +481,19 @@ int halo_slots(int q, int sign, int* slots)
     }
 }
 
+// LBM_OK if p is device memory of the handle's device (the halo copies are
+// device-to-device).
+int check_device_buffer(const lbm_ctx* h, const void* p)
+{
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, p);
+    if (e != cudaSuccess || attr.type != cudaMemoryTypeDevice || attr.device != h->device) {
+        cudaGetLastError();
+        return fail(LBM_EINVAL, "halo buffers must be device memory on the handle's device");
+    }
+    return LBM_OK;
+}
+
 // Halo buffer <-> plane z of the store: the f slots with e_z = sign, then the
 // g slots with e_z = sign, nx*ny elements each (one contiguous run per slot
 // and plane in the store). pack = store -> buffer.
@@ -1268,6 +1281,7 @@ int lbm_halo_pack(lbm_handle h, int phase, void* to_lower, void* to_upper)
     if (!h->store) return fail(LBM_ESTATE, "halo exchange before the store exists");
     if (phase != 0 && phase != 1) return fail(LBM_EINVAL, "phase must be 0 (before an odd step) or 1 (after it)");
     if (!to_lower || !to_upper) return fail(LBM_EINVAL, "null buffer");
+    if ((rc = check_device_buffer(h, to_lower)) || (rc = check_device_buffer(h, to_upper))) return rc;
     const int top = h->p.nz - 1;
     // phase 0: own boundary planes (plane 1: e_z = +1 slots; plane nz-2: e_z = -1)
     // phase 1: ghost planes (plane 0: e_z = -1 slots; plane nz-1: e_z = +1)
@@ -1283,6 +1297,7 @@ int lbm_halo_unpack(lbm_handle h, int phase, const void* from_lower, const void*
     if (!h->store) return fail(LBM_ESTATE, "halo exchange before the store exists");
     if (phase != 0 && phase != 1) return fail(LBM_EINVAL, "phase must be 0 (before an odd step) or 1 (after it)");
     if (!from_lower || !from_upper) return fail(LBM_EINVAL, "null buffer");
+    if ((rc = check_device_buffer(h, from_lower)) || (rc = check_device_buffer(h, from_upper))) return rc;
     const int top = h->p.nz - 1;
     // phase 0: into the ghost planes (plane 0: e_z = -1 slots; plane nz-1: e_z = +1)
     // phase 1: into the own boundary planes (plane 1: e_z = +1; plane nz-2: e_z = -1)

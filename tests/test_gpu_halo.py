@@ -100,3 +100,10 @@ def test_slab_mode_rejects_what_it_cannot_do():
     with pytest.raises(lbm.LbmError) as ei:
         lbm.lbm_halo_pack(s.h, 2, buf.ctypes.data, buf.ctypes.data)
     assert ei.value.code == -1
+    # host memory is refused before any copy
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_halo_pack(s.h, 0, buf.ctypes.data, buf.ctypes.data)
+    assert ei.value.code == -1
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_halo_unpack(s.h, 1, buf.ctypes.data, buf.ctypes.data)
+    assert ei.value.code == -1
