@@ -152,3 +152,34 @@ def test_64cubed_paper_parameters_against_the_oracle(oracle64p, storage):
         assert rep["pass"] and rep["selected"] == "fp16", rep
     else:
         assert not rep["pass"] and rep["selected"] == "fp32", rep
+
+
+# The 128^3 workload (both stencil pairs x Guo / Shan-Chen x Fr 0.5 / 0.1, Re 400,
+# 5000 steps, diagnostics every 50) against its stored FP64 oracle series.
+C1_NAMES = sorted(n for n in G.SERIES if n.startswith("c1_") and os.path.exists(G.path_of(n)))
+
+
+@pytest.mark.parametrize("name", C1_NAMES or ["c1_128_q19q7_guo_fr0.5"])
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_128cubed_workload_series_against_the_oracle(name, storage):
+    """FP32: E_k and E_p within 1e-5 at step 1000 (E_p relative to its window
+    maximum) and every diagnostics quantity within 1e-4 of the oracle over the
+    5000 steps; FP16: kept by the 1 % storage rule against the FP64 series."""
+    n, (qf, qg), forcing, Re, Fr, Sc, U0, steps, every, seed, amp = G.SERIES[name]
+    ref = G.read(name)
+    gpu = _gpu_series(n, f"{qf}x{qg}", forcing, Re, Fr, Sc, U0, steps, every, seed, amp, storage)
+    assert [d["step"] for d in gpu] == [d["step"] for d in ref]
+    rep = lbm.lbm_storage_rule(ref, gpu, storage, 0.01)
+    devs = {k: _max_dev(gpu, ref, k) for k in KEYS}
+    k1000 = 1000 // every
+    ep_max = max(d["Ep"] for d in ref[: k1000 + 1])
+    at1000 = {"Ek": abs(gpu[k1000]["Ek"] - ref[k1000]["Ek"]) / ref[k1000]["Ek"],
+              "Ep": abs(gpu[k1000]["Ep"] - ref[k1000]["Ep"]) / ep_max}
+    _report({"test": "128cubed_vs_oracle", "series": name, "storage": storage, "max_dev": devs,
+             "at_step_1000": at1000, "rule": rep})
+    if storage == "fp32":
+        assert at1000["Ek"] <= 1e-5 and at1000["Ep"] <= 1e-5, at1000
+        for k in KEYS:
+            assert devs[k] <= 1e-4, (k, devs)
+    else:
+        assert rep["pass"] and rep["selected"] == "fp16", rep
