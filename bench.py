@@ -9,13 +9,16 @@ diagnostics interval: 100 lattice updates plus one diagnostics evaluation,
 whose per-node part is fused into the first update (lbm_step_diagnostics).
 `value` is FP32-storage MLUPS over the timed steps; FP16/BF16 deviation
 storage (FP32 arithmetic) is timed the same way and reported beside it with
-its KE/PE/eps deviation from the FP32 run.
+the library's 16-bit storage rule applied to whole diagnostics series. The
+64-instance sweep of the batched drivers follows.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-Under torchrun (N > 1) each rank advances its own replica of the lattice
-(replicas only: the single-lattice workload has no data-parallel split
-without a halo exchange); `value` sums the ranks' node updates over the max
-per-rank time.
+       python bench.py --validation all      (the paper's own runs at 256^3)
+Under torchrun (N > 1) each rank advances its own replica of the headline
+lattice (the z-slab split with halo exchange exists, halo.py, but the
+headline number stays a per-GPU replica); `value` sums the ranks' node
+updates over the max per-rank time. The batch sweep is split over the ranks
+(lbm_batch_partition), the whole sweep's updates over the slowest rank.
 """
 from __future__ import annotations
 

@@ -1,7 +1,8 @@
 """Batched instances (many lattices advanced together) against single-lattice
-runs and the oracle, all three drivers, the 64-instance sweep, and the bounded grid
-barrier's timeout path (made to run out on purpose, with a short poll limit:
-the kernel returns an error status and the context stays usable)."""
+runs and the oracle, all three drivers, the 64-instance sweep, and the
+persistent driver's timeout path (its dependency waits made to run out on
+purpose, with a short poll limit: the kernel returns an error status and the
+context stays usable)."""
 import numpy as np
 import pytest
 
@@ -157,7 +158,8 @@ def test_sweep_64_instances_autotuned():
 
 def test_barrier_timeout_returns_an_error_and_the_context_survives():
     b = _batch(SMALL, "persistent", 5)
-    # one barrier arrival that never comes; each wait gives up after 2000 polls
+    # every dependency wait expects one completion more than exists; each
+    # wait gives up after 2000 polls
     lbm.lbm_batch_set_barrier_test(b, 1, 2000)
     lbm.lbm_batch_step(b, 5)
     with pytest.raises(lbm.LbmError) as ei:
