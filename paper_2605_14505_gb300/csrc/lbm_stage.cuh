@@ -10,7 +10,9 @@
 // segment is one bulk copy of W elements (even) or W + 16 elements from 8
 // before the tile to 8 after it (odd: the words k - 1 and k + 1 are read);
 // at either end of the row the 8-element pad wraps to the other end and is a
-// separate 16-byte copy. Warp 0 issues the copies of tile k + 1 into the
+// separate 16-byte copy. A tile that is a whole row (W = nx) needs no pads:
+// the words across its ends are the row's own, read modulo W from the staged
+// row, so every slot row is one copy on both AA steps. Warp 0 issues the copies of tile k + 1 into the
 // other half of a two-stage ring while the block computes tile k from shared
 // memory, so the DRAM latency is covered by the ring rather than by
 // registers held in flight. Results are stored straight to global memory as
@@ -144,7 +146,8 @@ __device__ __forceinline__ void stage_issue(const StageArgs& A, uint16_t* st, ui
     const uint32_t row = t / (uint32_t)A.ntx;
     const int y = (int)(row % (uint32_t)ny), z = (int)(row / (uint32_t)ny);
     const int xs = (int)xt * W;
-    const uint32_t row_bytes = (uint32_t)(ODD ? W + 2 * kStagePad : W) * 2u;
+    const bool whole = (W == nx);   // a whole row: no pads (read modulo W)
+    const uint32_t row_bytes = (uint32_t)((ODD && !whole) ? W + 2 * kStagePad : W) * 2u;
     if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)Q * row_bytes);
     __syncwarp();
     const uint16_t* base = static_cast<const uint16_t*>(A.f);
@@ -157,7 +160,7 @@ __device__ __forceinline__ void stage_issue(const StageArgs& A, uint16_t* st, ui
         zz = zz < 0 ? nz - 1 : (zz == nz ? 0 : zz);
         const uint16_t* src = base + (size_t)slot * A.geo.n3 + ((size_t)zz * ny + yy) * nx;
         uint16_t* dst = st + (size_t)r * RS;
-        if (!ODD) {
+        if (!ODD || whole) {
             bulk_copy_g2s(dst + kStagePad, src + xs, (uint32_t)W * 2u, bar);
         } else if (xs > 0 && xs + W < nx) {
             bulk_copy_g2s(dst, src + (xs - kStagePad), row_bytes, bar);
@@ -176,15 +179,21 @@ __device__ __forceinline__ uint32_t lds_word(const uint16_t* p)
 }
 
 // The pair's words of lattice L from its stage rows (rows = first row of L):
-// word p of the tile on the even step, word p - e_x on the odd step, with the
-// halves exchanged where the row wraps (as load_pair).
+// word p of the tile on the even step, word p - e_x on the odd step (modulo
+// the tile for a whole-row tile, W = nx), with the halves exchanged where the
+// row wraps (as load_pair).
 template <class L, bool ODD>
-__device__ __forceinline__ void stage_load(const uint16_t* rows, int RS, int p, const Seam& sm, uint32_t* w)
+__device__ __forceinline__ void stage_load(const uint16_t* rows, int RS, int W, bool whole, int p, const Seam& sm,
+                                           uint32_t* w)
 {
     sfor<0, L::kQ>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int ex = ODD ? L::ex(i) : 0;
-        w[i] = lds_word(rows + i * RS + kStagePad + 2 * p - 2 * ex);
+        int e = 2 * p - 2 * ex;
+        if constexpr (ex != 0) {
+            if (whole) e = (e < 0) ? e + W : (e >= W ? e - W : e);
+        }
+        w[i] = lds_word(rows + i * RS + kStagePad + e);
     });
     if constexpr (ODD) {
         if (sm.warp_first) {
@@ -248,8 +257,9 @@ __global__ void __launch_bounds__(128, kStageMinBlocks<P>) k_step_staged(const _
             const int x0 = (int)(t - row * (uint32_t)A.ntx) * W + 2 * p;
             const Seam sm(A.geo, x0);
             uint32_t wf[P::QF], wg[P::QG];
-            stage_load<typename P::LF, ODD>(st, RS, p, sm, wf);
-            stage_load<typename P::LG, ODD>(st + (size_t)P::QF * RS, RS, p, sm, wg);
+            const bool whole = (W == A.geo.nx);
+            stage_load<typename P::LF, ODD>(st, RS, W, whole, p, sm, wf);
+            stage_load<typename P::LG, ODD>(st + (size_t)P::QF * RS, RS, W, whole, p, sm, wg);
             collide_pair_words<P, FORCING, T>(wf, wg, A.ph);
             const int y = (int)(row % (uint32_t)A.geo.ny), z = (int)(row / (uint32_t)A.geo.ny);
             const PairAddr b(A.geo, (int)launder(x0), (int)launder(y), (int)launder(z));
