@@ -644,3 +644,31 @@ def test_gpu_spectrum_matches_host_spectrum():
     assert np.array_equal(k1, k2)
     assert np.allclose(E1, E2, rtol=1e-10, atol=1e-22)
     s.close()
+
+
+def test_nonfinite_state_is_reported():
+    """A NaN population (set on the host; NaN arithmetic does not fault) makes
+    every diagnostics entry point return LBM_ENONFINITE, with the record still
+    filled; the state and the context stay usable (re-initialised)."""
+    p = lattice_params(16, 8, 4, "27x19", "guo", 0.6, 0.6, 1e-5, -4.0)
+    s = gpu_sim(p)
+    rho, u, rp = I.random_fields(16, 8, 4, 21, 0.03, 0.01, 0.1)
+    s.init_fields(rho, u, rp)
+    f, g = s.populations()
+    f[3, 17] = np.nan
+    s.set_populations(f, g)
+    with pytest.raises(lbm.LbmError) as ei:
+        s.diagnostics()
+    assert ei.value.code == -5
+    d = s.diagnostics(allow_nonfinite=True)
+    assert not np.isfinite(d["mass_f"]) and d["step"] == 0
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_diagnostics_noalloc(s.h)
+    assert ei.value.code == -5
+    with pytest.raises(lbm.LbmError) as ei:
+        s.step_diagnostics(2)
+    assert ei.value.code == -5
+    s.init_fields(rho, u, rp)
+    s.step(3)
+    assert np.isfinite(s.diagnostics()["Ek"])
+    s.close()
