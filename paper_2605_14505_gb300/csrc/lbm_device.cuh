@@ -551,8 +551,22 @@ LBM_HD void collide_f(float* h, const Macro& m, const Phys& ph)
     // (eps ~ 1e-8), so the plain form w e.(rho v) / cs^2 would rescale the
     // momentum by ~(1 + 2 eps) every step (E_k off by ~5e-5 after 1000 steps).
     // The edge and corner pairs use the plain form; each axis pair takes the
-    // residual, so the momentum is exact up to the rounding of this sum.
-    float ox = 0.f, oy = 0.f, oz = 0.f;
+    // residual. That residual is formed without rounding: on the smooth,
+    // nearly two-dimensional Taylor-Green momenta the rounding errors of a
+    // plain FP32 running sum of the edge/corner parts (and even a single
+    // rounding of the exact residual, whose low bits sit near ties) follow
+    // the momentum, a relative momentum bias of ~6e-9 (D3Q19) / ~2e-9
+    // (D3Q27) per step that drifts E_k by ~5e-6 in 600 steps. So the sum is
+    // compensated (Knuth's TwoSum), the residual stays an unevaluated pair
+    // hi + lo, and the axis pair's new populations are formed so that each is
+    // rounded once (relax_axis).
+    float ox = 0.f, oy = 0.f, oz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    auto two_sum = [](float& s, float& c, float x) {
+        const float t = s + x;
+        const float z = t - s;
+        c += (s - (t - z)) + (x - z);
+        s = t;
+    };
     auto relax_pair = [&](auto mc, float ha) {
         constexpr int i = 2 * decltype(mc)::value + 1;
         constexpr int j = i + 1;
@@ -586,14 +600,51 @@ LBM_HD void collide_f(float* h, const Macro& m, const Phys& ph)
     sfor<3, kPairs<LF>>([&](auto mc) {
         constexpr int i = 2 * decltype(mc)::value + 1;
         const float ha = LF::w(i) * c1 * e_dot<LF, i>(mx, my, mzo);
-        if constexpr (LF::ex(i) != 0) ox += (float)LF::ex(i) * ha;
-        if constexpr (LF::ey(i) != 0) oy += (float)LF::ey(i) * ha;
-        if constexpr (LF::ez(i) != 0) oz += (float)LF::ez(i) * ha;
+        if constexpr (LF::ex(i) != 0) two_sum(ox, cx, (float)LF::ex(i) * ha);
+        if constexpr (LF::ey(i) != 0) two_sum(oy, cy, (float)LF::ey(i) * ha);
+        if constexpr (LF::ez(i) != 0) two_sum(oz, cz, (float)LF::ez(i) * ha);
         relax_pair(mc, ha);
     });
-    relax_pair(std::integral_constant<int, 0>{}, fmaf(0.5f, mx, -ox));    // slots 1, 2: +-x
-    relax_pair(std::integral_constant<int, 1>{}, fmaf(0.5f, my, -oy));    // slots 3, 4: +-y
-    relax_pair(std::integral_constant<int, 2>{}, fmaf(0.5f, mzo, -oz));   // slots 5, 6: +-z
+    // Axis pair with the odd part ha = hi + lo: the exact update
+    // h_i' = (sp + dp) / 2, dp = bgk(d, 2 ha) + 2 Fa, is
+    // hi + [sp / 2 + (delta - 1) n / 2 + (2 - delta) lo + Fa] with n = d - 2 hi
+    // (exact near equilibrium); the bracket is far below hi in magnitude, so
+    // its own roundings vanish in the final one. r0 = m / 2 - (sum) is exact
+    // whenever the sum lies between m / 4 and m (Sterbenz; it is ~m / 3 for
+    // D3Q19, ~5 m / 18 for D3Q27), and hi + lo = r0 - comp exactly (|r0| >>
+    // |comp|).
+    auto relax_axis = [&](auto mc, float r0, float comp) {
+        constexpr int i = 2 * decltype(mc)::value + 1;
+        constexpr int j = i + 1;
+        constexpr float w = LF::w(i);
+        constexpr int ez = LF::ez(i);
+        const float hi = r0 - comp;
+        const float lo = (r0 - hi) - comp;
+        const float eu = e_dot<LF, i>(vx, vy, vz);
+        const float em = e_dot<LF, i>(mx, my, mze);
+        const float hs = w * fmaf(c2 * em, eu, base);
+        float Fs = 0.f, Fa = 0.f;
+        if constexpr (FORCING == kHCZ) {
+            const float ps = 1.f + c2 * eu * eu - c0 * vsq;
+            const float pa = c1 * eu;
+            const float c = gF * c1 * w;
+            Fs = c * ((float)ez * pa - vz * ps);
+            Fa = c * ((float)ez * ps - vz * pa);
+        } else if constexpr (FORCING == kEDM) {
+            float ps = -c0 * dusq;
+            if constexpr (ez != 0) ps += c2 * du * (2.f * (float)ez * eu + du);
+            Fs = w * fmaf(m.drho, ps, ps);
+            Fa = (ez != 0) ? w * c1 * (float)ez * m.Fz : 0.f;
+        }
+        const float sp = bgk(h[i], 2.f * hs, dl) + 2.f * Fs;
+        const float n = h[j] - 2.f * hi;
+        const float t = fmaf(0.5f * dl, n, fmaf(-0.5f, n, fmaf(2.f - dl, lo, Fa)));   // delta kept exact
+        h[i] = hi + fmaf(0.5f, sp, t);
+        h[j] = -hi + fmaf(0.5f, sp, -t);
+    };
+    relax_axis(std::integral_constant<int, 0>{}, fmaf(0.5f, mx, -ox), cx);    // slots 1, 2: +-x
+    relax_axis(std::integral_constant<int, 1>{}, fmaf(0.5f, my, -oy), cy);    // slots 3, 4: +-y
+    relax_axis(std::integral_constant<int, 2>{}, fmaf(0.5f, mzo, -oz), cz);   // slots 5, 6: +-z
 }
 
 // g collision (Eqs. 11, 12, 14, 15): g_eq = (rho' + rho0) Theta(u), S_i = w_i (-u_z beta).
