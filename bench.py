@@ -46,7 +46,7 @@ WORKLOAD = "stratified TGV 256^3, D3Q27xD3Q19, velocity-shift (Shan-Chen) forcin
 # (dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture, mean of
 # an even and an odd launch), with the fingerprint of the kernel sources the
 # capture ran; reported as null once the sources differ from it.
-NCU_TRAFFIC = {"fingerprint": "3d288dbe775b4ed6", "fp32": 6115758976, "fp16": 3028256128, "bf16": 3028244224}
+NCU_TRAFFIC = {"fingerprint": "86b1945ef20a280a", "fp32": 6117004672, "fp16": 3028206336, "bf16": 3028232064}
 
 
 def source_fingerprint() -> str:
@@ -71,10 +71,10 @@ def source_fingerprint() -> str:
 # DRAM bytes per step of the 64-instance sweep, by driver (ncu, on the step
 # kernels of the fingerprint above): the per-instance driver over 128
 # graph-replayed steps as one profiler range (--replay-mode app-range, all
-# streams together: 736.1 GB in 128 steps, the instances' own L2 reuse
-# included); the persistent driver from its full capture (one launch of 4
-# steps: exactly the algorithmic 5.95 GB per step).
-NCU_BATCH_DRAM = {"fingerprint": "3d288dbe775b4ed6", "instances": 5750517354, "persistent": 5947972250}
+# streams together: 739.3 GB in 128 steps, the instances' own L2 reuse
+# included); the persistent driver from one launch of 4 steps (5.96 GB per
+# step, the algorithmic 5.95 GB).
+NCU_BATCH_DRAM = {"fingerprint": "86b1945ef20a280a", "instances": 5775440492, "persistent": 5958025216}
 
 
 def ncu_traffic(storage: str):

@@ -412,7 +412,12 @@ struct FastMoments {
         m.rho = 1.f + drho;
         m.irho = 1.f / m.rho;
         m.dirho = m.irho - 1.f;
-        m.rho_p = fast_div(a + ph.kappa * jz * m.irho, 1.f + 0.5f * ph.kappa * ph.G * m.irho);
+        // rho' = a + d, d = kappa j_z / rho - num x / (1 + x), as node_macro
+        // forms it: a coherent rounding of the tiny x would compound over the
+        // steps where the storage's own rounding averages out
+        const float kj = ph.kappa * jz * m.irho;
+        const float x = 0.5f * ph.kappa * ph.G * m.irho;
+        m.rho_p = a + fmaf(-(a + kj), fast_div(x, 1.f + x), kj);
         m.Fz = -ph.G * m.rho_p;
         m.ux = jx * m.irho;
         m.uy = jy * m.irho;
