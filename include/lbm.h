@@ -356,15 +356,17 @@ enum lbm_pairing { LBM_PAIRING_OFF = 0, LBM_PAIRING_ALL = 1, LBM_PAIRING_EVEN = 
 int lbm_set_pairing(lbm_handle h, int mode);
 
 /* Tile staging (FP16/BF16 storage, nx a multiple of 64; off by default):
- * the step kernel is persistent; for each tile of W nodes of an
- * x-row (W = 256, 128 or 64, the largest dividing nx) warp 0 issues one bulk
- * asynchronous copy (cp.async.bulk, completion on an mbarrier) per slot row
- * into shared memory, one tile ahead of the compute, and two nodes per thread
- * update from there; the per-node arithmetic and the stores are those of the
- * two-nodes-per-thread kernel (Eqs. 5-18 as in lbm_step). enable = 0 returns
- * to the kernels selected by lbm_set_pairing. Every wait on a copy is
- * bounded; a wait that runs out makes the next lbm_synchronize return
- * LBM_ETIMEOUT (the lattice state is then not valid). */
+ * the step kernel is persistent and warp-specialised. For each tile of W
+ * nodes of an x-row (W = 256, 128 or 64, the largest dividing nx) a producer
+ * warp issues one bulk asynchronous copy (cp.async.bulk, completion on an
+ * mbarrier) per slot row into a ring of shared-memory stages; W / 64 consumer
+ * warps, two nodes per thread, load their words from a stage, hand it back
+ * (a second mbarrier per stage) and update; the per-node arithmetic and the
+ * stores are those of the two-nodes-per-thread kernel (Eqs. 5-18 as in
+ * lbm_step). enable = 0 returns to the kernels selected by lbm_set_pairing.
+ * Every wait on a copy or a stage is bounded; a wait that runs out makes the
+ * next lbm_synchronize return LBM_ETIMEOUT (the lattice state is then not
+ * valid). */
 int lbm_set_tile_staging(lbm_handle h, int enable);
 
 /* *width = the tile width the staged kernel uses for this lattice, or 0 if
@@ -373,14 +375,16 @@ int lbm_set_tile_staging(lbm_handle h, int enable);
 int lbm_uses_tile_staging(lbm_handle h, int* width);
 
 /* Test hook for the bounded waits of tile staging: with extra_tx_bytes > 0
- * each block also waits, after its copies of a tile have landed, on a barrier
- * of its own that expects extra_tx_bytes which no copy delivers, so that wait
- * runs out; every wait polls at most spin_limit times. A block whose wait ran
- * out raises the error flag and then waits for its own bulk copies still in
- * flight with a fixed limit of its own (about 0.3-1 s, independent of
- * spin_limit) before it exits, so no copy writes shared memory after the
- * block has ended. (0, 1 << 22) restores normal operation. Errors:
- * LBM_EINVAL for spin_limit = 0 or extra_tx_bytes >= 2^20. */
+ * each consumer warp also waits, after the copies of its first tile have
+ * landed, on a barrier of its own that expects extra_tx_bytes which no copy
+ * delivers, so that wait runs out; every wait polls at most spin_limit times.
+ * A warp whose wait ran out raises the error flag and stops; the producer
+ * warp, whose wait for the stages to be handed back then runs out too, stops
+ * issuing and waits for its bulk copies still in flight with a fixed limit of
+ * its own (about 0.3-1 s, independent of spin_limit) before it exits, so no
+ * copy writes shared memory after the block has ended. (0, 1 << 22) restores
+ * normal operation. Errors: LBM_EINVAL for spin_limit = 0 or
+ * extra_tx_bytes >= 2^20. */
 int lbm_set_stage_test(lbm_handle h, unsigned extra_tx_bytes, unsigned spin_limit);
 
 /* ---- z-slab decomposition (one lattice over several GPUs) ----------------

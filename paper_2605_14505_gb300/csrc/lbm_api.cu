@@ -385,14 +385,14 @@ cudaError_t launch_staged(lbm_ctx* h, int odd, int W, cudaStream_t s)
         if (e == cudaSuccess) e = cudaFuncSetAttribute(h->ks->staged[h->p.forcing][odd ^ 1],
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int occ = 0;
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, W / 2, smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, stage_threads(W), smem);
         if (e != cudaSuccess) return e;
         if (occ < 1) return cudaErrorInvalidConfiguration;
         const size_t cap = (size_t)(h->num_sms > 0 ? h->num_sms : 1) * (size_t)occ;
         h->stage_grid = (int)(a.ntiles < cap ? a.ntiles : cap);
     }
     void* args[] = {&a};
-    return cudaLaunchKernel(k, dim3((unsigned)h->stage_grid), dim3((unsigned)(W / 2)), args, smem, s);
+    return cudaLaunchKernel(k, dim3((unsigned)h->stage_grid), dim3((unsigned)stage_threads(W)), args, smem, s);
 }
 
 cudaError_t launch_step(lbm_ctx* h, int odd, cudaStream_t s)

@@ -1,32 +1,39 @@
 // 16-bit storage, two nodes per thread, with the populations of each tile
 // brought into shared memory by bulk asynchronous copies (cp.async.bulk,
-// completion counted on an mbarrier) one tile ahead of the compute.
+// completion counted on an mbarrier) ahead of the compute, by a warp of its
+// own.
 //
 // The store is in half-row order (row_pos): word k of a row holds nodes k and
-// k + nx / 2. A tile is W = 2 * blockDim.x consecutive elements of one x-row
-// (y, z), the words of blockDim.x pairs; thread p takes word xs / 2 + p. For
-// every slot the AA step reads one row segment: slot i of row (y, z) on the
-// even step, slot opp(i) of row (y - e_y, z - e_z) on the odd step. Each such
-// segment is one bulk copy of W elements (even) or W + 16 elements from 8
-// before the tile to 8 after it (odd: the words k - 1 and k + 1 are read);
-// at either end of the row the 8-element pad wraps to the other end and is a
-// separate 16-byte copy. A tile that is a whole row (W = nx) needs no pads:
-// the words across its ends are the row's own, read modulo W from the staged
-// row, so every slot row is one copy on both AA steps. Warp 0 issues the copies of tile k + 1 into the
-// other half of a two-stage ring while the block computes tile k from shared
-// memory, so the DRAM latency is covered by the ring rather than by
-// registers held in flight. Results are stored straight to global memory as
-// in k_step2 (aligned 32-bit words). Blocks are persistent: block b takes
-// tiles b, b + grid, ...
+// k + nx / 2. A tile is W consecutive elements of one x-row (y, z), the words
+// of W / 2 pairs; consumer thread p takes word xs / 2 + p. For every slot the
+// AA step reads one row segment: slot i of row (y, z) on the even step, slot
+// opp(i) of row (y - e_y, z - e_z) on the odd step. Each such segment is one
+// bulk copy of W elements. The odd step also reads the words k - 1 and k + 1:
+// a tile that is a whole row (W = nx) finds the words across its ends in the
+// row itself, read modulo W from the staged row; a narrower tile gets 8
+// elements on either side (wrapping at the row's ends) as two plain 16-byte
+// loads per slot row, which the producer lanes store beside the copy.
 //
-// Every mbarrier wait is bounded (spin_limit polls). A wait that runs out
-// raises *err; the block then drains: it waits for the barriers of the copies
-// it has issued, with its own fixed limit (kStageDrainPolls, independent of
-// spin_limit), and returns, so a barrier that cannot complete ends the kernel
-// and no bulk copy is still writing shared memory when the block exits. The
-// test hook's phantom bytes are counted on a barrier of their own that no
-// copy signals, so the real copies' barriers always complete and the drain
-// observes every copy landing.
+// Warp specialisation: a block is W / 64 consumer warps and one producer
+// warp around a ring of kStageRing stages. Stage s has a "full" barrier (the
+// producer's expected bytes, completed by the copies) and an "empty" barrier
+// (one arrival per consumer warp). A consumer warp waits for full[s], loads
+// its pair's words into registers, arrives on empty[s] and only then
+// collides and stores, so the producer refills the stage while the
+// consumers compute; no block-wide barrier is taken per tile and each
+// consumer warp runs at its own pace. Results are stored straight to global
+// memory as in k_step2 (aligned 32-bit words). Blocks are persistent: block b
+// takes tiles b, b + grid, ...
+//
+// Every mbarrier wait is bounded (spin_limit polls). A consumer warp whose
+// wait runs out raises *err and returns; the producer, whose empty-barrier
+// wait then runs out too, raises *err and stops issuing. Whatever happens,
+// the producer waits for the full barriers of the last stages it filled
+// (with a fixed limit of its own, kStageDrainPolls) before it returns: the
+// block's shared memory lives until its last thread exits, so no bulk copy
+// is still writing it then. The test hook's phantom bytes are counted on a
+// barrier of their own that no copy signals, so the real copies' barriers
+// always complete and the drain observes every copy landing.
 #pragma once
 
 #include "lbm_kernels.cuh"
@@ -38,7 +45,7 @@ struct StageArgs {
     void* g;
     Geometry geo;
     Phys ph;
-    int W;                  // tile width in nodes: 2 * blockDim.x, divides nx, multiple of 8
+    int W;                  // tile width in nodes: a multiple of 64 that divides nx
     int ntx;                // nx / W
     uint32_t ntiles;        // ntx * ny * nz
     int* err;               // set to 1 when a wait gives up
@@ -51,12 +58,20 @@ struct StageArgs {
 constexpr uint32_t kStageDrainPolls = 1u << 22;
 
 constexpr int kStagePad = 8;   // staged row element j holds row element xs - 8 + j
+#ifndef LBM_STAGE_RING
+#define LBM_STAGE_RING 2
+#endif
+constexpr int kStageRing = LBM_STAGE_RING;  // stages of the ring
 
-// Shared-memory bytes of one block: two stages of Q rows of W + 16 elements,
-// three mbarriers (one per stage, one for the test hook), Q row codes.
+// Threads of a block for tile width W: one consumer thread per word, one producer warp.
+__host__ __device__ constexpr int stage_threads(int W) { return W / 2 + 32; }
+
+// Shared-memory bytes of one block: kStageRing stages of Q rows of W + 16
+// elements, the mbarriers (full and empty per stage, one for the test hook),
+// Q row codes.
 __host__ __device__ constexpr size_t stage_smem_bytes(int q, int W)
 {
-    return (size_t)2 * q * (W + 2 * kStagePad) * 2 + 24 + (size_t)q * 4;
+    return (size_t)kStageRing * q * (W + 2 * kStagePad) * 2 + 8 * (2 * kStageRing + 1) + (size_t)q * 4;
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
@@ -73,6 +88,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
@@ -133,7 +153,13 @@ __device__ __forceinline__ uint32_t stage_row_code(int r)
     return (uint32_t)slot | (uint32_t)(dy + 1) << 8 | (uint32_t)(dz + 1) << 10;
 }
 
-// Warp 0: the copies of tile t into one stage, counted on `bar`.
+// The producer warp: the copies of tile t into one stage, counted on `bar`.
+// Each slot row's tile body is one bulk copy. Where the odd step needs the
+// words across the ends of a tile narrower than the row, the 8-element pads
+// on either side (wrapping at the row's ends) are two plain 16-byte loads per
+// slot row, stored to the stage by the producer lanes; those stages' barrier
+// expects one arrival from each producer lane besides the copies' bytes, so
+// a lane's arrival releases its pad stores to the consumers.
 template <class P, bool ODD>
 __device__ __forceinline__ void stage_issue(const StageArgs& A, uint16_t* st, uint64_t* bar, const uint32_t* code,
                                             uint32_t t)
@@ -146,30 +172,46 @@ __device__ __forceinline__ void stage_issue(const StageArgs& A, uint16_t* st, ui
     const uint32_t row = t / (uint32_t)A.ntx;
     const int y = (int)(row % (uint32_t)ny), z = (int)(row / (uint32_t)ny);
     const int xs = (int)xt * W;
-    const bool whole = (W == nx);   // a whole row: no pads (read modulo W)
-    const uint32_t row_bytes = (uint32_t)((ODD && !whole) ? W + 2 * kStagePad : W) * 2u;
-    if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)Q * row_bytes);
-    __syncwarp();
+    const bool pads = ODD && W != nx;   // a whole row reads across its ends modulo W
     const uint16_t* base = static_cast<const uint16_t*>(A.f);
-    for (int r = lane; r < Q; r += 32) {
+    auto src_row = [&](int r) {
         const uint32_t c = code[r];
         const int slot = (int)(c & 0xffu);
         int yy = y + (int)((c >> 8) & 3u) - 1;
         int zz = z + (int)((c >> 10) & 3u) - 1;
         yy = yy < 0 ? ny - 1 : (yy == ny ? 0 : yy);
         zz = zz < 0 ? nz - 1 : (zz == nz ? 0 : zz);
-        const uint16_t* src = base + (size_t)slot * A.geo.n3 + ((size_t)zz * ny + yy) * nx;
-        uint16_t* dst = st + (size_t)r * RS;
-        if (!ODD || whole) {
-            bulk_copy_g2s(dst + kStagePad, src + xs, (uint32_t)W * 2u, bar);
-        } else if (xs > 0 && xs + W < nx) {
-            bulk_copy_g2s(dst, src + (xs - kStagePad), row_bytes, bar);
-        } else {
-            // head and tail pads wrap at the ends of the row
-            bulk_copy_g2s(dst, src + (xs > 0 ? xs - kStagePad : nx - kStagePad), kStagePad * 2u, bar);
-            bulk_copy_g2s(dst + kStagePad, src + xs, (uint32_t)W * 2u, bar);
-            bulk_copy_g2s(dst + kStagePad + W, src + (xs + W < nx ? xs + W : 0), kStagePad * 2u, bar);
+        return base + (size_t)slot * A.geo.n3 + ((size_t)zz * ny + yy) * nx;
+    };
+    // pads first, all of a lane's loads in flight together (two rows per lane)
+    static_assert(Q <= 64, "two stage rows per producer lane");
+    uint4 head[2], tail[2];
+    if (pads) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int r = lane + 32 * k;
+            if (r < Q) {
+                const uint16_t* src = src_row(r);
+                head[k] = *reinterpret_cast<const uint4*>(src + (xs > 0 ? xs - kStagePad : nx - kStagePad));
+                tail[k] = *reinterpret_cast<const uint4*>(src + (xs + W < nx ? xs + W : 0));
+            }
         }
+    }
+    if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)Q * (uint32_t)W * 2u);
+    __syncwarp();
+    for (int r = lane; r < Q; r += 32)
+        bulk_copy_g2s(st + (size_t)r * RS + kStagePad, src_row(r) + xs, (uint32_t)W * 2u, bar);
+    if (pads) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int r = lane + 32 * k;
+            if (r < Q) {
+                uint16_t* dst = st + (size_t)r * RS;
+                *reinterpret_cast<uint4*>(dst) = head[k];
+                *reinterpret_cast<uint4*>(dst + kStagePad + W) = tail[k];
+            }
+        }
+        mbar_arrive(bar);
     }
 }
 
@@ -178,22 +220,33 @@ __device__ __forceinline__ uint32_t lds_word(const uint16_t* p)
     return *reinterpret_cast<const uint32_t*>(p);
 }
 
+// Element offsets, within a staged row, of the words a consumer thread reads:
+// o[0] = word p - 1, o[1] = word p + 1, o[2] = word p (of the tile). For a
+// whole-row tile (W = nx, a power of two here) the words across the ends are
+// the row's own, modulo W; otherwise the pads hold them.
+struct StageOff {
+    int o[3];
+    __device__ __forceinline__ StageOff(int W, bool whole, int p)
+    {
+        const int m = whole ? W - 1 : -1;   // all ones: no wrap
+        o[0] = kStagePad + ((2 * p - 2) & m);
+        o[1] = kStagePad + ((2 * p + 2) & m);
+        o[2] = kStagePad + 2 * p;
+    }
+};
+
 // The pair's words of lattice L from its stage rows (rows = first row of L):
-// word p of the tile on the even step, word p - e_x on the odd step (modulo
-// the tile for a whole-row tile, W = nx), with the halves exchanged where the
-// row wraps (as load_pair).
+// word p of the tile on the even step, word p - e_x on the odd step, with the
+// halves exchanged where the row wraps (as load_pair).
 template <class L, bool ODD>
-__device__ __forceinline__ void stage_load(const uint16_t* rows, int RS, int W, bool whole, int p, const Seam& sm,
+__device__ __forceinline__ void stage_load(const uint16_t* rows, int RS, const StageOff& so, const Seam& sm,
                                            uint32_t* w)
 {
     sfor<0, L::kQ>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int ex = ODD ? L::ex(i) : 0;
-        int e = 2 * p - 2 * ex;
-        if constexpr (ex != 0) {
-            if (whole) e = (e < 0) ? e + W : (e >= W ? e - W : e);
-        }
-        w[i] = lds_word(rows + i * RS + kStagePad + e);
+        constexpr int k = ex == 1 ? 0 : ex == -1 ? 1 : 2;
+        w[i] = lds_word(rows + i * RS + so.o[k]);
     });
     if constexpr (ODD) {
         if (sm.warp_first) {
@@ -211,69 +264,103 @@ __device__ __forceinline__ void stage_load(const uint16_t* rows, int RS, int W, 
     }
 }
 
+// Collision form and occupancy per pair, from sweeps at 256^3 (FP16, ms per
+// step even / odd): D3Q27xD3Q19 holds each node's FP32 values in an array
+// (collide_pair_words, 128 registers, three blocks of four consumer warps
+// per SM: 0.495 / 0.499) rather than streaming them from the packed words
+// (96 registers, four blocks: 0.545 / 0.561; 80 registers with a one-stage
+// ring, five blocks: 0.505 / 0.550); the smaller pairs stream (D3Q19xD3Q7
+// 0.302 / 0.305 against 0.320 / 0.334 with the array form).
 template <class P>
-constexpr int kStageMinBlocks = (P::QF + P::QG <= 34) ? 6 : 4;
+constexpr bool kStageStream = (P::QF + P::QG <= 34);
+template <class P>
+constexpr int kStageMinBlocks = kStageStream<P> ? 6 : 3;
 
 template <class P, int FORCING, class T, bool ODD>
-__global__ void __launch_bounds__(128, kStageMinBlocks<P>) k_step_staged(const __grid_constant__ StageArgs A)
+__global__ void __launch_bounds__(160, kStageMinBlocks<P>) k_step_staged(const __grid_constant__ StageArgs A)
 {
     constexpr int Q = P::QF + P::QG;
+    constexpr uint32_t S = kStageRing;
     extern __shared__ __align__(128) unsigned char smem[];
     const int W = A.W, RS = W + 2 * kStagePad;
+    const int nc = W / 2;   // consumer threads
     uint16_t* stages = reinterpret_cast<uint16_t*>(smem);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)2 * Q * RS * 2);
-    uint32_t* code = reinterpret_cast<uint32_t*>(bar + 3);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * Q * RS * 2);
+    uint64_t* empty = full + S;
+    uint64_t* hook = empty + S;
+    uint32_t* code = reinterpret_cast<uint32_t*>(hook + 1);
     for (int r = (int)threadIdx.x; r < Q; r += (int)blockDim.x) code[r] = stage_row_code<P, ODD>(r);
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_init(&bar[2], 1);
-        // test hook: phase 0 of bar[2] expects bytes that no copy delivers
-        if (A.extra_tx) mbar_arrive_expect_tx(&bar[2], A.extra_tx);
+        // full: the expected bytes' arrival, and one per producer lane where it stores pads
+        const uint32_t full_count = (ODD && W != A.geo.nx) ? 33u : 1u;
+        for (uint32_t s = 0; s < S; ++s) {
+            mbar_init(&full[s], full_count);
+            mbar_init(&empty[s], (uint32_t)nc / 32u);
+        }
+        mbar_init(hook, 1);
+        // test hook: phase 0 of its barrier expects bytes that no copy delivers
+        if (A.extra_tx) mbar_arrive_expect_tx(hook, A.extra_tx);
         fence_mbarrier_init();
     }
     __syncthreads();
     if (blockIdx.x >= A.ntiles) return;
-    const bool producer = threadIdx.x < 32;
-    if (producer) stage_issue<P, ODD>(A, stages, &bar[0], code, blockIdx.x);
+    const int lane = (int)(threadIdx.x & 31);
+
+    if ((int)threadIdx.x >= nc) {
+        // producer: tile j of this block goes to stage j % S, use j / S
+        uint32_t j = 0;
+        bool ok = true;
+        for (uint32_t t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++j) {
+            const uint32_t s = j % S, u = j / S;
+            if (j >= S) {
+                // the consumers have loaded the stage's previous use
+                ok = __all_sync(0xffffffffu, mbar_wait(&empty[s], (u - 1u) & 1u, A.spin_limit));
+                if (!ok) break;
+            }
+            fence_proxy_async_smem();
+            stage_issue<P, ODD>(A, stages + (size_t)s * Q * RS, &full[s], code, t);
+        }
+        if (!ok && lane == 0) atomicExch(A.err, 1);
+        // the copies of the last stages filled land before the block can exit
+        for (uint32_t i = j > S ? j - S : 0u; i < j; ++i) mbar_wait(&full[i % S], (i / S) & 1u, kStageDrainPolls);
+        return;
+    }
 
     unsigned short* fb = static_cast<unsigned short*>(A.f);
     unsigned short* gb = static_cast<unsigned short*>(A.g);
     const int p = (int)threadIdx.x;
-    uint32_t k = 0;
-    for (uint32_t t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++k) {
-        const uint32_t s = k & 1u;
-        const uint32_t tn = t + gridDim.x;
-        if (producer && tn < A.ntiles) {
-            // stage s ^ 1 was last read for tile k - 1, before the barrier that ended it
-            fence_proxy_async_smem();
-            stage_issue<P, ODD>(A, stages + (size_t)(s ^ 1u) * Q * RS, &bar[s ^ 1u], code, tn);
-        }
-        bool ok = mbar_wait(&bar[s], (k >> 1) & 1u, A.spin_limit);
-        if (A.extra_tx && ok) ok = mbar_wait(&bar[2], 0u, A.spin_limit);
-        if (ok) {
-            const uint16_t* st = stages + (size_t)s * Q * RS;
-            const uint32_t row = t / (uint32_t)A.ntx;
-            const int x0 = (int)(t - row * (uint32_t)A.ntx) * W + 2 * p;
-            const Seam sm(A.geo, x0);
-            uint32_t wf[P::QF], wg[P::QG];
-            const bool whole = (W == A.geo.nx);
-            stage_load<typename P::LF, ODD>(st, RS, W, whole, p, sm, wf);
-            stage_load<typename P::LG, ODD>(st + (size_t)P::QF * RS, RS, W, whole, p, sm, wg);
-            collide_pair_words<P, FORCING, T>(wf, wg, A.ph);
-            const int y = (int)(row % (uint32_t)A.geo.ny), z = (int)(row / (uint32_t)A.geo.ny);
-            const PairAddr b(A.geo, (int)launder(x0), (int)launder(y), (int)launder(z));
-            store_pair<typename P::LF, ODD>(fb, A.geo.n3, b, sm, wf);
-            store_pair<typename P::LG, ODD>(gb, A.geo.n3, b, sm, wg);
-        }
-        if (__syncthreads_or(!ok)) {
-            // a wait ran out: report, wait for this block's copies in flight
-            // (the two stage barriers; the hook's barrier has none), stop
-            if (threadIdx.x == 0) atomicExch(A.err, 1);
-            mbar_wait(&bar[s], (k >> 1) & 1u, kStageDrainPolls);
-            if (tn < A.ntiles) mbar_wait(&bar[s ^ 1u], ((k + 1) >> 1) & 1u, kStageDrainPolls);
+    const StageOff so(W, W == A.geo.nx, p);
+    uint32_t j = 0;
+    for (uint32_t t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++j) {
+        const uint32_t s = j % S, u = j / S;
+        bool ok = mbar_wait(&full[s], u & 1u, A.spin_limit);
+        if (A.extra_tx && j == 0 && ok) ok = mbar_wait(hook, 0u, A.spin_limit);
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) atomicExch(A.err, 1);
             return;
         }
+        const uint32_t row = t / (uint32_t)A.ntx;
+        const int x0 = (int)(t - row * (uint32_t)A.ntx) * W + 2 * p;
+        const Seam sm(A.geo, x0);
+        uint32_t wf[P::QF], wg[P::QG];
+        {
+            const uint16_t* st = stages + (size_t)s * Q * RS;
+            stage_load<typename P::LF, ODD>(st, RS, so, sm, wf);
+            stage_load<typename P::LG, ODD>(st + (size_t)P::QF * RS, RS, so, sm, wg);
+        }
+        // the warp's words are in registers: hand the stage back
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if constexpr (kStageStream<P>) {
+            collide_half_stream<P, FORCING, T, 0>(wf, wg, A.ph);
+            collide_half_stream<P, FORCING, T, 1>(wf, wg, A.ph);
+        } else {
+            collide_pair_words<P, FORCING, T>(wf, wg, A.ph);
+        }
+        const int y = (int)(row % (uint32_t)A.geo.ny), z = (int)(row / (uint32_t)A.geo.ny);
+        const PairAddr b(A.geo, (int)launder(x0), (int)launder(y), (int)launder(z));
+        store_pair<typename P::LF, ODD>(fb, A.geo.n3, b, sm, wf);
+        store_pair<typename P::LG, ODD>(gb, A.geo.n3, b, sm, wg);
     }
 }
 

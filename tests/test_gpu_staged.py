@@ -1,5 +1,6 @@
 """The tile-staged step kernel (16-bit storage; rows brought into shared
-memory by bulk asynchronous copies on an mbarrier, two nodes per thread):
+memory by a producer warp's bulk asynchronous copies on mbarriers, two nodes
+per consumer thread):
 against the direct-load pair kernel, against the oracle, at the bench size by
 sampling, and its bounded waits (made to run out on purpose with a test hook
 that expects more bytes than the copies deliver: the kernel returns, the next
@@ -140,10 +141,11 @@ def test_staged_wait_timeout_returns_an_error_and_the_context_survives():
     lbm.lbm_set_tile_staging(s.h, True)
     s.init_tgv(seed=1, noise_amp=1e-3)
     assert lbm.lbm_uses_tile_staging(s.h) == 64
-    # each block also waits on a barrier that expects 16 bytes no copy
+    # each consumer warp also waits on a barrier that expects 16 bytes no copy
     # delivers; with 64 polls per wait even the waits on the real copies
-    # usually run out first. Either way the block drains its own copies (a
-    # fixed limit of its own) before it returns.
+    # usually run out first. Either way the consumers stop, the producer's
+    # wait for the stages to come back runs out, and the producer waits for
+    # its own copies (a fixed limit of its own) before the block returns.
     for spin in (64, 20000):
         lbm.lbm_set_stage_test(s.h, 16, spin)
         s.step(2)
