@@ -83,13 +83,31 @@ __global__ void __launch_bounds__(256, 3) k_batch_variant(BatchArgs A)
 }
 
 // Nodes [n0, n1) of one instance, consecutive nodes on consecutive threads.
+// A thread's coordinates are divided out of its first node index once and
+// then advanced by the block size (dx, dy) with carries, instead of two
+// divisions and two remainders by the run-time sizes per node (dx < nx, so x
+// carries into y at most once; y carries into z once per plane advanced).
 template <class P, int FORCING, bool ODD>
 __device__ __forceinline__ void flow_nodes(const BatchInstance& I, uint32_t n0, uint32_t n1)
 {
-    for (uint32_t n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
-        int x, y, z;
-        node_xyz(I.geo, n, x, y, z);
+    uint32_t n = n0 + threadIdx.x;
+    if (n >= n1) return;
+    int x, y, z;
+    node_xyz(I.geo, n, x, y, z);
+    const int nx = I.geo.nx, ny = I.geo.ny;
+    const int dy = (int)(blockDim.x / (unsigned)nx), dx = (int)blockDim.x - dy * nx;
+    for (; n < n1; n += blockDim.x) {
         batch_node<P, FORCING, ODD>(I, x, y, z);
+        x += dx;
+        y += dy;
+        if (x >= nx) {
+            x -= nx;
+            ++y;
+        }
+        while (y >= ny) {
+            y -= ny;
+            ++z;
+        }
     }
 }
 
