@@ -267,7 +267,7 @@ __device__ __forceinline__ void stage_load(const uint16_t* rows, int RS, const S
 // Collision form and occupancy per pair, from sweeps at 256^3 (FP16, ms per
 // step even / odd): D3Q27xD3Q19 holds each node's FP32 values in an array
 // (collide_pair_words, 128 registers, three blocks of four consumer warps
-// per SM: 0.495 / 0.499) rather than streaming them from the packed words
+// per SM: 0.490 / 0.498) rather than streaming them from the packed words
 // (96 registers, four blocks: 0.545 / 0.561; 80 registers with a one-stage
 // ring, five blocks: 0.505 / 0.550); the smaller pairs stream (D3Q19xD3Q7
 // 0.302 / 0.305 against 0.320 / 0.334 with the array form).
