@@ -266,12 +266,14 @@ __device__ __forceinline__ void update_node(void* fv, void* gv, const Geometry& 
 // D3Q27xD3Q19 lattice, 2% faster for FP32 Shan-Chen and 16% for FP16 with one
 // node per thread than the unconstrained allocation (up to 124 registers).
 // D3Q27xD3Q27, whose 54 values per node spill up to 180 bytes at that cap,
-// takes two (<= 128 registers).
+// takes two (<= 128 registers). Pairs of at most 26 values (D3Q19xD3Q7,
+// D3Q15xD3Q7) fit four blocks (64 registers) without spilling: D3Q19xD3Q7
+// FP32 at 256^3 0.516 against 0.543 ms per step with three.
 #ifndef LBM_STEP_MINBLOCKS
 #define LBM_STEP_MINBLOCKS 3
 #endif
 template <class P>
-constexpr int kStepMinBlocks = (P::QF + P::QG > 46) ? 2 : LBM_STEP_MINBLOCKS;
+constexpr int kStepMinBlocks = (P::QF + P::QG > 46) ? 2 : (P::QF + P::QG <= 26) ? 4 : LBM_STEP_MINBLOCKS;
 // One AA step for every node of one lattice.
 template <class P, int FORCING, class T, bool ODD>
 __global__ void __launch_bounds__(256, kStepMinBlocks<P>) k_step(StepArgs args)
@@ -388,9 +390,14 @@ struct Seam {
 // against 0.269 ms at 256^3).
 __device__ __forceinline__ uint32_t seam_word(uint32_t w, uint32_t sel) { return __byte_perm(w, 0u, sel); }
 
+// Streaming (evict-first) word loads that ask L2 for the whole 256-byte
+// block, as the FP32 loads do: D3Q19xD3Q7 FP16 at 256^3 0.2638 against
+// 0.2694 ms per step with plain loads, D3Q27xD3Q19 unchanged (0.4536 ms).
 __device__ __forceinline__ uint32_t ld_word(const unsigned short* p)
 {
-    return *reinterpret_cast<const unsigned int*>(p);
+    uint32_t v;
+    asm volatile("ld.global.cs.L2::256B.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
 }
 __device__ __forceinline__ void st_word(unsigned short* p, uint32_t w)
 {
