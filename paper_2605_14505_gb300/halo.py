@@ -25,7 +25,8 @@ from __future__ import annotations
 class LibrarySlab:
     """One slab of the CUDA library: a Simulation (already initialised with its
     own planes and the two neighbouring ones) switched to slab mode. The AA
-    parity is counted from the initialisation (natural layout)."""
+    parity is the handle's step count since its initialisation (natural layout
+    after an even count), so a slab may be wrapped after it has stepped."""
 
     def __init__(self, sim):
         import torch
@@ -37,7 +38,7 @@ class LibrarySlab:
         self.sim = sim
         lbm.lbm_set_slab(sim.h, True)
         self.halo_bytes = lbm.lbm_halo_bytes(sim.h)
-        self.odd = 0
+        self.odd = lbm.lbm_step_count(sim.h) & 1
 
     def new_buffer(self):
         return self._torch.empty(self.halo_bytes, dtype=self._torch.uint8, device="cuda")
