@@ -122,13 +122,20 @@ LBM_HD void sfor(F&& f)
 // ---------------------------------------------------------------------------
 template <class T>
 __device__ __forceinline__ float ld_pop(const T* p);
-// FP32 populations: streaming (evict-first) loads that also ask L2 to fetch
-// the whole 256-byte block around the address. A warp's row segment is 128
-// bytes and the next warp reads the next one, so the second half arrives
-// early: 0.9087 against 0.9121-0.9128 ms per step at 256^3 (D3Q27xD3Q19,
-// two boxes); the 16-bit word loads gained nothing from it. The block lies
-// in the same mapped page as the address, so the hint never reaches past
-// the allocation's pages.
+// Population loads are streaming (evict-first) and ask L2 to fetch the whole
+// 256-byte block around the address. A warp's row segment is 128 bytes in
+// FP32 (64 in 16-bit storage) and the next warps read the next ones, so the
+// rest of the block arrives early: FP32 D3Q27xD3Q19 at 256^3 0.9087 against
+// 0.9121-0.9128 ms per step (two boxes), D3Q19xD3Q7 0.5433 against 0.5509;
+// the one-node 16-bit kernel 0.3-0.8 % faster. The block lies in the same
+// mapped page as the address, so the hint never reaches past the
+// allocation's pages.
+__device__ __forceinline__ uint16_t ld_u16_stream(const void* p)
+{
+    uint16_t v;
+    asm volatile("ld.global.cs.L2::256B.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+}
 template <>
 __device__ __forceinline__ float ld_pop<float>(const float* p)
 {
@@ -137,11 +144,14 @@ __device__ __forceinline__ float ld_pop<float>(const float* p)
     return v;
 }
 template <>
-__device__ __forceinline__ float ld_pop<__half>(const __half* p) { return __half2float(__ldcs(p)); }
+__device__ __forceinline__ float ld_pop<__half>(const __half* p)
+{
+    return __half2float(__ushort_as_half(ld_u16_stream(p)));
+}
 template <>
 __device__ __forceinline__ float ld_pop<__nv_bfloat16>(const __nv_bfloat16* p)
 {
-    return __bfloat162float(__ldcs(p));
+    return __bfloat162float(__ushort_as_bfloat16(ld_u16_stream(p)));
 }
 template <class T>
 __device__ __forceinline__ void st_pop(T* p, float v);

@@ -381,8 +381,6 @@ struct Seam {
     }
 };
 
-// Loads default-cached: the odd step writes each word back shortly after
-// reading it, and a word still in L2 takes the write without a miss.
 // A seam slot's word in a warp that holds a seam lane: one byte permute with
 // the lane's own selector, which exchanges the halves on the seam lane and
 // keeps the word elsewhere (a select between the word and its permutation
