@@ -46,7 +46,7 @@ WORKLOAD = "stratified TGV 256^3, D3Q27xD3Q19, velocity-shift (Shan-Chen) forcin
 # (dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture, mean of
 # an even and an odd launch), with the fingerprint of the kernel sources the
 # capture ran; reported as null once the sources differ from it.
-NCU_TRAFFIC = {"fingerprint": "1fe0574732e9b307", "fp32": 6116773760, "fp16": 3027854848, "bf16": 3027871744}
+NCU_TRAFFIC = {"fingerprint": "18dee20ce526b74c", "fp32": 6116793728, "fp16": 3027879552, "bf16": 3028134272}
 
 
 def source_fingerprint() -> str:
@@ -71,10 +71,10 @@ def source_fingerprint() -> str:
 # DRAM bytes per step of the 64-instance sweep, by driver (ncu, on the step
 # kernels of the fingerprint above): the per-instance driver over 128
 # graph-replayed steps as one profiler range (--replay-mode app-range, all
-# streams together: 739.8 GB in 128 steps, the instances' own L2 reuse
+# streams together: 739.9 GB in 128 steps, the instances' own L2 reuse
 # included); the persistent driver from one launch of 4 steps (5.97 GB per
 # step, the algorithmic 5.95 GB).
-NCU_BATCH_DRAM = {"fingerprint": "1fe0574732e9b307", "instances": 5779801898, "persistent": 5970983808}
+NCU_BATCH_DRAM = {"fingerprint": "18dee20ce526b74c", "instances": 5780572946, "persistent": 5971162432}
 
 
 def ncu_traffic(storage: str):
